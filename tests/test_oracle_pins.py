@@ -1,0 +1,574 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: a closed form, an
+invariant, a library routine (scipy's linear interpolation, numpy's piecewise-linear
+interp), the masks printed in the paper (tests/golden/), brute force on tiny inputs, or
+finite differences.  A plausible slip in the oracle (a dropped term, a wrong sign or
+index, a transposed operand) makes at least one of them fail.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import phantoms as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+OPS = ["central", "sobel3d", "zucker_hummel"]
+
+
+def _vol(arr, vmax=1.0):
+    return oracle.OracleVolume(arr, vmax)
+
+
+def _field(n, fn):
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    return fn(x.astype(np.float64), y.astype(np.float64), z.astype(np.float64))
+
+
+# ------------------------------------------------------------------ trilinear (§3.4)
+def test_trilinear_exact_on_trilinear_fields():
+    """Eq. 2 / §3.4: trilinear interpolation reproduces any trilinear field exactly."""
+    rng = np.random.default_rng(11)
+    c = rng.uniform(-2, 2, 8)
+    f = lambda x, y, z: (c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * y + c[5] * y * z
+                         + c[6] * x * z + c[7] * x * y * z)
+    ov = _vol(_field((8, 8, 8), f))
+    ts = np.arange(0, 57) / 8.0  # every 1/8-voxel position of [0, 7]
+    worst = 0.0
+    for z in ts[::3]:
+        for y in ts[::2]:
+            for x in ts:
+                worst = max(worst, abs(oracle.sample(ov, [x, y, z]) - f(x, y, z)))
+    assert worst < 1e-12
+
+
+def test_trilinear_matches_scipy_linear_interpolation():
+    """Against scipy.ndimage.map_coordinates(order=1, mode='nearest') (clamp-to-edge)."""
+    from scipy.ndimage import map_coordinates
+
+    rng = np.random.default_rng(12)
+    arr = rng.uniform(0, 1, (5, 7, 6))  # (nz, ny, nx)
+    ov = _vol(arr)
+    pts = rng.uniform(-1.5, 8.0, (400, 3))  # many outside the box
+    ref = map_coordinates(arr, [pts[:, 2], pts[:, 1], pts[:, 0]], order=1, mode="nearest")
+    got = np.array([oracle.sample(ov, p) for p in pts])
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+def test_value_decode_units():
+    """Reading R1: s = raw / value_max for integer storage."""
+    arr = np.full((3, 3, 3), 4095, np.uint16)
+    assert oracle.sample(_vol(arr, 4095.0), [1.0, 1.0, 1.0]) == 1.0
+    arr8 = np.full((3, 3, 3), 51, np.uint8)
+    assert abs(oracle.sample(_vol(arr8, 255.0), [0.3, 1.2, 1.9]) - 0.2) < 1e-15
+
+
+# ------------------------------------------------------- gradient operators (§3.5)
+@pytest.mark.parametrize("op", OPS)
+def test_operators_exact_on_linear_fields(op):
+    rng = np.random.default_rng(21)
+    b = rng.uniform(-1, 1, 3)
+    a0 = 0.3
+    n = (9, 10, 11)
+    ov = _vol(_field(n, lambda x, y, z: a0 + b[0] * x + b[1] * y + b[2] * z))
+    for _ in range(200):
+        p = [rng.uniform(1.0, n[i] - 2.0) for i in range(3)]  # every tap inside the box
+        g = oracle.gradient(ov, op, p)
+        np.testing.assert_allclose(g, b, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_operators_zero_on_constant_fields(op):
+    rng = np.random.default_rng(22)
+    exact = _vol(np.full((6, 5, 4), 0.375))  # every product and sum exact in FP64
+    inexact = _vol(np.full((6, 5, 4), 0.37))
+    for _ in range(100):
+        p = rng.uniform(-1.0, 6.0, 3)  # includes the clamped border
+        if op != "zucker_hummel":  # irrational weights round
+            assert np.all(oracle.gradient(exact, op, p) == 0.0)
+        assert np.all(np.abs(oracle.gradient(inexact, op, p)) < 1e-15)
+
+
+def _impulse_kernel(op):
+    """3x3x3 kernel of each component, read off by impulses at an integer point."""
+    k = np.zeros((3, 3, 3, 3))  # component, dx, dy, dz
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                arr = np.zeros((5, 5, 5))
+                arr[2 + dz, 2 + dy, 2 + dx] = 1.0
+                g = oracle.gradient(_vol(arr), op, [2.0, 2.0, 2.0])
+                k[:, dx + 1, dy + 1, dz + 1] = g
+    return k
+
+
+def _read_sobel_golden():
+    comps = {}
+    cur, plane = None, None
+    with open(os.path.join(GOLDEN, "sobel3d_masks.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("component"):
+                cur = line.split()[1]
+                comps[cur] = []
+            elif line.startswith("plane"):
+                comps[cur].append([])
+            else:
+                comps[cur][-1].append([float(v) for v in line.split()])
+    return {c: np.array(v) for c, v in comps.items()}  # each (plane, row, col)
+
+
+def test_sobel_matches_printed_masks():
+    """Eq. 4: the x mask exactly as printed; y and z under the rotation reading (R7)."""
+    gold = _read_sobel_golden()
+    k = _impulse_kernel("sobel3d") * 44.0  # undo the 1/(2*22) scale
+    # x component: plane = x offset; rows/cols = the two other axes (mask is symmetric)
+    np.testing.assert_allclose(k[0], gold["x"], atol=1e-12)
+    # y component: printed planes are x slices, rows run from y+1 (top) to y-1 (bottom),
+    # columns are z; + on the +1 side.
+    y = np.zeros((3, 3, 3))
+    for a in range(3):
+        for r in range(3):
+            for c in range(3):
+                y[a, 2 - r, c] = gold["y"][a, r, c]
+    np.testing.assert_allclose(k[1], y, atol=1e-12)
+    # z component: printed planes are x slices, rows are y, columns run z-1 .. z+1.
+    np.testing.assert_allclose(k[2], gold["z"], atol=1e-12)
+    # the printed weights 1, 3, 6 sum to 22 per side
+    assert gold["x"][2].sum() == 22.0
+
+
+def test_central_difference_matches_printed_stencil():
+    """Eq. 3: delta = V(P + e) - V(P - e), scaled by 1/2."""
+    k = _impulse_kernel("central") * 2.0
+    with open(os.path.join(GOLDEN, "central_difference.txt")) as fh:
+        rows = [l.split() for l in fh if l.strip() and not l.startswith("#")]
+    expect = np.zeros((3, 3, 3, 3))
+    for ax, off, w in rows:
+        a = "xyz".index(ax)
+        idx = [1, 1, 1]
+        idx[a] += int(off)
+        expect[a][tuple(idx)] = float(w)
+    np.testing.assert_allclose(k, expect, atol=1e-12)
+
+
+def test_zucker_hummel_weights_are_direction_cosines():
+    k = _impulse_kernel("zucker_hummel")
+    s_side = 1 + 4 / math.sqrt(2) + 4 / math.sqrt(3)
+    for b in (-1, 0, 1):
+        for c in (-1, 0, 1):
+            w = 1.0 / math.sqrt(1 + b * b + c * c) / (2 * s_side)
+            assert abs(k[0, 2, b + 1, c + 1] - w) < 1e-14
+            assert abs(k[0, 0, b + 1, c + 1] + w) < 1e-14
+            assert k[0, 1, b + 1, c + 1] == 0.0
+    # 54 non-zero taps over the three components, 6 for central differences (§4)
+    assert np.count_nonzero(np.abs(k) > 0) == 54
+    assert np.count_nonzero(np.abs(_impulse_kernel("central")) > 0) == 6
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_operators_reflection_and_permutation_symmetry(op):
+    rng = np.random.default_rng(23)
+    arr = rng.uniform(0, 1, (7, 7, 7))
+    ov = _vol(arr)
+    ovr = _vol(arr[:, :, ::-1].copy())  # mirror x
+    ovt = _vol(np.transpose(arr, (1, 2, 0)).copy())  # new (z,y,x) = old (y,x,z): axes permuted
+    for _ in range(40):
+        p = rng.uniform(0, 6, 3)
+        g = oracle.gradient(ov, op, p)
+        gr = oracle.gradient(ovr, op, [6.0 - p[0], p[1], p[2]])
+        np.testing.assert_allclose(gr, [-g[0], g[1], g[2]], atol=1e-13)
+        # permuted volume: new x = old z, new y = old x, new z = old y
+        gt = oracle.gradient(ovt, op, [p[2], p[0], p[1]])
+        np.testing.assert_allclose(gt, [g[2], g[0], g[1]], atol=1e-13)
+
+
+def test_zucker_hummel_normal_is_radial_on_a_smooth_sphere():
+    """On a radially symmetric bump the outward normal is radial, error O(h^2)."""
+    errs = []
+    for sigma in (3.0, 6.0):
+        n = int(8 * sigma) + 1
+        c = (n - 1) / 2.0
+        arr = _field((n, n, n), lambda x, y, z: np.exp(-((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+                                                        / (2 * sigma * sigma)))
+        ov = _vol(arr)
+        rng = np.random.default_rng(24)
+        worst = 0.0
+        for _ in range(60):
+            v = rng.normal(size=3)
+            v /= np.linalg.norm(v)
+            p = c + sigma * v
+            g = oracle.gradient(ov, "zucker_hummel", p)
+            N = -g / np.linalg.norm(g)
+            worst = max(worst, math.acos(min(1.0, float(N @ v))))
+        errs.append(worst)
+    assert errs[0] < 0.06
+    assert errs[1] < errs[0] / 2.5  # shrinks roughly with h^2 / sigma^2
+
+
+# --------------------------------------------------------- transfer function (§3.7)
+def test_tf_exact_at_knots_and_linear_between():
+    rng = np.random.default_rng(31)
+    tf = rng.uniform(0, 1, (17, 4))
+    for i in range(17):
+        out, _ = oracle.tf_lookup(tf, i / 16.0)
+        np.testing.assert_allclose(out, tf[i], atol=1e-15)
+    for i in range(16):
+        for w in (0.25, 0.5, 0.9):
+            out, slope = oracle.tf_lookup(tf, (i + w) / 16.0)
+            np.testing.assert_allclose(out, (1 - w) * tf[i] + w * tf[i + 1], atol=1e-14)
+            np.testing.assert_allclose(slope, (tf[i + 1] - tf[i]) * 16.0, atol=1e-12)
+    s = rng.uniform(-0.5, 1.5, 200)
+    for c in range(4):
+        ref = np.interp(s * 16.0, np.arange(17), tf[:, c])  # clamps at both ends
+        got = np.array([oracle.tf_lookup(tf, v)[0][c] for v in s])
+        np.testing.assert_allclose(got, ref, atol=1e-14)
+
+
+# -------------------------------------------------------------- shading (§3.8)
+def test_shading_listing_and_phong_closed_forms():
+    rgb = np.array([0.2, 0.5, 0.9])
+    up = np.array([0.0, 0.0, 1.0])
+    # Listing 3: illum = dot(livec, norm) with a white light -> kd-only Phong on the lit side
+    L = np.array([0.6, 0.0, 0.8])
+    c = oracle.shade(up, L, up, np.ones(3), ka=0.0, kd=1.0, ks=0.0)
+    np.testing.assert_allclose(c, [0.8] * 3, atol=1e-15)
+    # light behind the surface: ambient only (diffuse clamped at 0, no specular)
+    c = oracle.shade(up, -L, up, rgb, ka=0.1, kd=0.7, ks=0.2)
+    np.testing.assert_allclose(c, 0.1 * rgb, atol=1e-15)
+    # N = L = V: diffuse 1, mirror direction = V, specular 1
+    c = oracle.shade(up, up, up, rgb)
+    np.testing.assert_allclose(c, rgb * 0.8 + 0.2, atol=1e-15)
+    # specular from the textbook reflection vector (Householder mirror of L about N)
+    V = np.array([-0.6, 0.0, 0.8])
+    Rm = -(np.eye(3) - 2 * np.outer(up, up)) @ L  # reflection of L about the normal
+    spec = max(0.0, Rm @ V) ** 20
+    c = oracle.shade(up, L, V, rgb)
+    np.testing.assert_allclose(c, rgb * (0.1 + 0.7 * 0.8) + 0.2 * spec, atol=1e-14)
+    # zero normal (inside homogeneous material, §3.6): ambient only
+    c = oracle.shade(np.zeros(3), L, up, rgb)
+    np.testing.assert_allclose(c, 0.1 * rgb, atol=1e-15)
+
+
+# ------------------------------------------------------------ compositing (Eq. 6)
+def test_front_to_back_equals_printed_back_to_front_recursion():
+    rng = np.random.default_rng(41)
+    for n in (1, 2, 7, 40):
+        a = rng.uniform(0, 0.4, n)
+        c = rng.uniform(0, 1, (n, 3))
+        out, used = oracle.composite(a, c, ert=2.0)  # never terminates
+        assert used == n
+        C = np.zeros(3)  # Eq. 6 from the back: C_out = C_in (1 - a) + C(X) a
+        for k in range(n - 1, -1, -1):
+            C = C * (1 - a[k]) + c[k] * a[k]
+        np.testing.assert_allclose(out[:3], C, atol=1e-14)
+        np.testing.assert_allclose(out[3], 1 - np.prod(1 - a), atol=1e-14)
+
+
+def test_early_termination_stops_at_first_opaque_sample():
+    a = np.full(50, 0.3)
+    c = np.ones((50, 3))
+    out, used = oracle.composite(a, c, ert=0.99)
+    k = math.ceil(math.log(0.01) / math.log(0.7))
+    assert used == k
+    np.testing.assert_allclose(out[3], 1 - 0.7 ** k, atol=1e-14)
+    # identical to the untruncated result up to that sample
+    full, _ = oracle.composite(a[:k], c[:k], ert=2.0)
+    np.testing.assert_allclose(out, full, atol=1e-15)
+
+
+@pytest.mark.parametrize("alpha_entry", [0.01, 0.05, 0.2])
+def test_homogeneous_slab_closed_form(alpha_entry):
+    """A constant volume: g = 0, c = ka * rgb, A = 1 - (1 - a)^K, C = ka * rgb * A."""
+    n = 16
+    arr = np.full((n, n, n), 0.5)
+    tf = np.zeros((3, 4))
+    tf[:, :3] = [0.4, 0.6, 0.8]
+    tf[:, 3] = alpha_entry
+    cam = P.ortho_axis_camera((n, n, n), 20, 20, "+z", ortho_height=float(n))
+    pr = oracle.make_params(step=0.5, grad="sobel3d", ert_threshold=0.99)
+    img, counts, total = oracle.render(_vol(arr), tf, cam, pr)
+    K = round((n - 1) / 0.5)
+    kend = min(K, math.ceil(math.log(0.01) / math.log(1 - alpha_entry)))
+    hit = counts > 0
+    assert hit.sum() > 0 and np.all(counts[hit] == kend)
+    A = 1 - (1 - alpha_entry) ** kend
+    np.testing.assert_allclose(img[hit][:, 3], A, atol=1e-14)
+    expect = np.broadcast_to(0.1 * np.array([0.4, 0.6, 0.8]) * A, img[hit][:, :3].shape)
+    np.testing.assert_allclose(img[hit][:, :3], expect, rtol=0, atol=1e-14)
+    assert np.all(img[~hit] == 0.0)
+
+
+# -------------------------------------------------------------- ray setup (§3.3)
+def test_sphere_workload_ray_count():
+    """64^3 volume, 256^2 orthographic view on +z: 252^2 rays with K = 126 (chord 63)."""
+    w = P.workload_sphere_64()
+    pr = oracle.make_params(step=0.5)
+    hits = 0
+    Ks = set()
+    for py in range(256):
+        for px in (0, 1, 2, 100, 253, 254, 255):
+            hit, o, d, tn, K = oracle.ray(w["camera"], pr, (64, 64, 64), px, py)
+            if hit and K > 0:
+                Ks.add(K)
+                if px == 100:
+                    hits += 1
+            # pixel centres land on 1/4-voxel positions: x = (px + 1/2) / 4 - 1/2
+            assert o[0] == np.float32((px + 0.5) / 4 - 0.5)
+            assert o[1] == np.float32(31.5 + (1 - (2 * py + 1) / 256) * 32)  # py = 0 at the top
+    assert Ks == {126} and hits == 252
+    ov = _vol(w["volume"], 255.0)
+    _, counts, total = oracle.render(ov, w["tf"], w["camera"], pr)
+    assert (counts > 0).sum() == 252 * 252 and total == 252 * 252 * 126
+
+
+def _inside(p, lo, hi, tol):
+    return np.all(p >= lo - tol) and np.all(p <= hi + tol)
+
+
+def test_perspective_rays_against_point_in_box_brute_force():
+    shp = (40, 30, 25)
+    rng = np.random.default_rng(51)
+    lo = np.zeros(3)
+    hi = np.array(shp, float) - 1
+    for trial in range(6):
+        cam = P.orbit_camera(shp, 64, 48, rng.uniform(0, 6.28), rng.uniform(-1, 1), 40.0,
+                             radius_diag=rng.uniform(0.3, 2.0))
+        pr = oracle.make_params(step=float(rng.choice([0.5, 0.75, 1.3])))
+        for _ in range(150):
+            px, py = int(rng.integers(0, 64)), int(rng.integers(0, 48))
+            hit, o, d, tn, K = oracle.ray(cam, pr, shp, px, py)
+            o64, d64, st = o.astype(np.float64), d.astype(np.float64), float(pr.step)
+            assert abs(np.linalg.norm(d64) - 1) < 1e-6
+            if hit and K > 0:
+                for k in range(K):
+                    assert _inside(o64 + (tn + (k + 0.5) * st) * d64, lo, hi, 1e-3)
+                assert not _inside(o64 + (tn + (K + 0.5) * st) * d64, lo, hi, -1e-3)
+                if tn > 0:
+                    assert not _inside(o64 + (tn - 0.5 * st) * d64, lo, hi, -1e-3)
+            else:
+                ts = np.arange(0.0, 6 * np.linalg.norm(hi), 0.05)
+                pts = o64[None, :] + ts[:, None] * d64[None, :]
+                inside = np.all((pts >= lo + 1e-3) & (pts <= hi - 1e-3), axis=1)
+                # a ray shorter than half a step may hit with K = 0; otherwise no point is inside
+                assert not inside.any() or (hit and K == 0)
+
+
+# -------------------------------------------------- whole image, independent loop
+def _np_ray(cam, shp, px, py, step, clip_lo, clip_hi):
+    """Independent float32 restatement of reading R2-R4 in numpy."""
+    f32 = np.float32
+    eye = np.array(cam["eye"], f32)
+    tgt = np.array(cam["target"], f32)
+    up = np.array(cam["up"], f32)
+
+    def dot(a, b):
+        r = f32(a[0] * b[0])
+        r = f32(r + f32(a[1] * b[1]))
+        return f32(r + f32(a[2] * b[2]))
+
+    def norm(v):
+        l = np.sqrt(dot(v, v), dtype=f32)
+        return np.array([v[0] / l, v[1] / l, v[2] / l], f32)
+
+    def cross(a, b):
+        return np.array([f32(a[1] * b[2]) - f32(a[2] * b[1]), f32(a[2] * b[0]) - f32(a[0] * b[2]),
+                         f32(a[0] * b[1]) - f32(a[1] * b[0])], f32)
+
+    fwd = norm(tgt - eye)
+    right = norm(cross(fwd, up))
+    upv = cross(right, fwd)
+    half = float(f32(cam["ortho_height"]) / f32(2)) if cam["ortho"] else math.tan(
+        cam["fov_y_deg"] * math.pi / 360.0)
+    ay, ax = f32(half), f32(half * cam["width"] / cam["height"])
+    sx = f32(f32(2 * px + 1) / f32(cam["width"])) - f32(1)
+    sy = f32(1) - f32(f32(2 * py + 1) / f32(cam["height"]))
+    u, v = f32(sx * ax), f32(sy * ay)
+    if cam["ortho"]:
+        o = np.array([f32(f32(eye[a] + f32(u * right[a])) + f32(v * upv[a])) for a in range(3)], f32)
+        d = fwd
+    else:
+        o = eye
+        d = norm(np.array([f32(f32(fwd[a] + f32(u * right[a])) + f32(v * upv[a])) for a in range(3)], f32))
+    lo = np.maximum(np.array(clip_lo, f32), f32(0))
+    hi = np.minimum(np.array(clip_hi, f32), np.array(shp, f32) - f32(1))
+    tn, tf = f32(0), f32(np.inf)
+    for a in range(3):
+        if d[a] == 0:
+            if o[a] < lo[a] or o[a] > hi[a]:
+                return None
+        else:
+            t0, t1 = f32((lo[a] - o[a]) / d[a]), f32((hi[a] - o[a]) / d[a])
+            tn = max(tn, min(t0, t1))
+            tf = min(tf, max(t0, t1))
+    if not tf >= tn:
+        return None
+    return o, d, tn
+
+
+def _np_render(arr, vmax, tf, cam, step, op, ert, clip_lo=(-1e30,) * 3, clip_hi=(1e30,) * 3):
+    """Naive dense march: no box clipping, alpha forced to 0 outside the box, scipy
+    trilinear (clamp-to-edge), numpy interp for the transfer function, taps summed."""
+    from scipy.ndimage import map_coordinates
+
+    nz, ny, nx = arr.shape
+    shp = (nx, ny, nz)
+    a = arr.astype(np.float64) / vmax
+    N = tf.shape[0]
+    lo = np.maximum(np.array(clip_lo, np.float64), 0)
+    hi = np.minimum(np.array(clip_hi, np.float64), np.array(shp, np.float64) - 1)
+
+    def tri(q):
+        q = np.atleast_2d(q)
+        return map_coordinates(a, [q[:, 2], q[:, 1], q[:, 0]], order=1, mode="nearest")
+
+    taps = {"central": ([(1, 0, 0)], lambda b, c: 1.0),
+            "sobel3d": ([(1, b, c) for b in (-1, 0, 1) for c in (-1, 0, 1)],
+                        lambda b, c: [[1, 3, 1], [3, 6, 3], [1, 3, 1]][b + 1][c + 1]),
+            "zucker_hummel": ([(1, b, c) for b in (-1, 0, 1) for c in (-1, 0, 1)],
+                              lambda b, c: 1 / math.sqrt(1 + b * b + c * c))}[op]
+
+    def grad(p):
+        g = np.zeros(3)
+        for ax in range(3):
+            o1, o2 = (ax + 1) % 3, (ax + 2) % 3
+            offs, ws = [], []
+            for (_, b, c) in taps[0]:
+                w = taps[1](b, c)
+                for sgn in (1, -1):
+                    off = np.zeros(3)
+                    off[ax], off[o1], off[o2] = sgn, b, c
+                    offs.append(off)
+                    ws.append(sgn * w)
+            ws = np.array(ws)
+            side_sum = ws[ws > 0].sum()
+            g[ax] = (ws * tri(p[None, :] + np.array(offs))).sum() / (2 * side_sum)
+        return g
+
+    img = np.zeros((cam["height"], cam["width"], 4))
+    eye = np.array(cam["eye"], np.float32).astype(np.float64)
+    for py in range(cam["height"]):
+        for px in range(cam["width"]):
+            r = _np_ray(cam, shp, px, py, step, clip_lo, clip_hi)
+            if r is None:
+                continue
+            o, d, tn = (x.astype(np.float64) if hasattr(x, "astype") else x for x in r)
+            C, T = np.zeros(3), 1.0
+            for k in range(0, 4 * int(np.linalg.norm(hi) / step) + 8):
+                p = o + (float(tn) + (k + 0.5) * step) * d
+                if not (np.all(p >= lo) and np.all(p <= hi)):
+                    continue  # alpha = 0 outside the box
+                s = tri(p)[0]
+                rgba = np.array([np.interp(s * (N - 1), np.arange(N), tf[:, ch]) for ch in range(4)])
+                al = rgba[3]
+                if al == 0:
+                    continue
+                g = grad(p)
+                gn = np.linalg.norm(g)
+                Nn = -g / gn if gn > 1e-6 else np.zeros(3)
+                L = eye - p
+                L /= np.linalg.norm(L)
+                V = -d if cam["ortho"] else (eye - p) / np.linalg.norm(eye - p)
+                nl = Nn @ L
+                diff = max(nl, 0.0)
+                spec = 0.0
+                if nl > 0:
+                    R = 2 * nl * Nn - L
+                    spec = max(R @ V, 0.0) ** 20
+                c = rgba[:3] * (0.1 + 0.7 * diff) + 0.2 * spec
+                C += T * al * c
+                T *= 1 - al
+                if 1 - T >= ert:
+                    break
+            img[py, px, :3] = C
+            img[py, px, 3] = 1 - T
+    return img
+
+
+@pytest.mark.parametrize("op,ortho", [("central", True), ("sobel3d", False), ("zucker_hummel", False)])
+def test_whole_image_brute_force_8cube(op, ortho):
+    arr = P.random_volume(61, (8, 8, 8), np.uint8, 255.0)
+    tf = P.tf_random(62, 16, alpha_max=0.35, zero_below=3)
+    shp = (8, 8, 8)
+    if ortho:
+        cam = P.orbit_camera(shp, 12, 10, 0.7, 0.4, ortho=True, ortho_height=12.0)
+    else:
+        cam = P.orbit_camera(shp, 12, 10, 2.1, -0.3, 40.0, radius_diag=1.2)
+    pr = oracle.make_params(step=0.5, grad=op, ert_threshold=0.95)
+    img, counts, _ = oracle.render(_vol(arr, 255.0), tf, cam, pr)
+    ref = _np_render(arr, 255.0, tf.astype(np.float64), cam, 0.5, op, 0.95)
+    assert (counts > 0).sum() > 30
+    np.testing.assert_allclose(img, ref, rtol=0, atol=1e-10)
+
+
+def test_clip_box_cuts_the_volume():
+    """§3.6: a clip box restricts sampling; gradients still read voxels outside it."""
+    arr = P.random_volume(63, (8, 8, 8), np.uint8, 255.0)
+    tf = P.tf_random(64, 16, alpha_max=0.3)
+    cam = P.orbit_camera((8, 8, 8), 10, 10, 0.4, 0.5, 40.0, radius_diag=1.5)
+    lo, hi = (1.5, 0.0, 2.0), (6.0, 5.5, 7.0)
+    pr = oracle.make_params(step=0.5, grad="sobel3d", ert_threshold=0.99, clip_lo=lo, clip_hi=hi)
+    img, _, _ = oracle.render(_vol(arr, 255.0), tf, cam, pr)
+    ref = _np_render(arr, 255.0, tf.astype(np.float64), cam, 0.5, "sobel3d", 0.99, lo, hi)
+    np.testing.assert_allclose(img, ref, rtol=0, atol=1e-10)
+
+
+# --------------------------------------------------------- reverse mode vs FD
+def _loss(ov, tf, cam, pr, wts):
+    img, _, _ = oracle.render(ov, tf, cam, pr)
+    return float((img * wts).sum())
+
+
+@pytest.mark.parametrize("op", ["central", "zucker_hummel"])
+def test_backward_oracle_matches_central_finite_differences(op):
+    n = 6
+    rng = np.random.default_rng(71)
+    arr = rng.uniform(0.15, 0.85, (n, n, n))
+    tf = P.tf_random(72, 8, alpha_max=0.4).astype(np.float64)
+    cam = P.orbit_camera((n, n, n), 7, 6, 0.9, 0.35, 40.0, radius_diag=1.3)
+    pr = oracle.make_params(step=0.5, grad=op, ert_threshold=0.97)
+    wts = rng.uniform(-1, 1, (cam["height"], cam["width"], 4))
+    ov = _vol(arr)
+    gv, gt = oracle.render_backward(ov, tf, cam, pr, wts)
+    h = 1e-6
+
+    def check(get, set_, analytic):
+        x0 = get()
+        set_(x0 + h)
+        fp = _loss(ov, tf, cam, pr, wts)
+        set_(x0 - h)
+        fm = _loss(ov, tf, cam, pr, wts)
+        set_(x0)
+        f0 = _loss(ov, tf, cam, pr, wts)
+        right, left = (fp - f0) / h, (f0 - fm) / h
+        if abs(right - left) > 1e-4 * (1 + abs(right)):
+            return None  # a kink (TF knot, N.L = 0, early-termination flip): skip
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - analytic) <= 1e-5 * (1 + abs(fd)), (fd, analytic)
+        return True
+
+    checked = 0
+    flat = ov.arr.reshape(-1)
+    for i in range(flat.size):
+        def get(i=i):
+            return flat[i]
+
+        def set_(v, i=i):
+            flat[i] = v
+        checked += bool(check(get, set_, gv.reshape(-1)[i]))
+    for i in range(tf.size):
+        tff = tf.reshape(-1)
+
+        def get(i=i):
+            return tff[i]
+
+        def set_(v, i=i):
+            tff[i] = v
+        checked += bool(check(get, set_, gt.reshape(-1)[i]))
+    assert checked > 0.9 * (flat.size + tf.size)
+    assert np.abs(gv).max() > 0 and np.abs(gt).max() > 0
