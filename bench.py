@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 volume ray caster.
+
+Default workload: the 512x512x361 uint16 CT-like phantom (seed 2) rendered at 1920x1080
+with a perspective camera, step 0.5, Zucker-Hummel gradients, empty-space skipping and
+early termination.  One step = the whole hot path on device-resident inputs:
+vr_upload_volume (padded copy + brick min/max) -> vr_set_transfer_function (+ brick
+visibility) -> vr_set_camera -> vr_render (ray setup + fused march).
+
+Metric: Gsamples/s, where a sample is one t_k the plain method marches (every sample up to
+early termination, whether or not empty-space skipping visited it); the count comes from
+the kernel's own counters and is checked against the FP64 oracle by the GPU tests.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FP32 operations per sample (see the design notes): every visited sample
+# pays the trilinear value, the transfer-function lerp and the sample position; a shaded
+# sample adds the operator gradient (blended over the cell), the normalisation, Phong and
+# the compositing update.
+FLOPS_VISIT = 34
+FLOPS_SHADE = {"central": 96, "sobel3d": 392, "zucker_hummel": 392}
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["ct", "ellipsoids", "sphere"], default="ct")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e / cpu legs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(name):
+    import phantoms as P
+
+    if name == "ct":
+        return P.workload_ct()
+    if name == "ellipsoids":
+        return P.workload_ellipsoids_256()
+    return P.workload_sphere_64()
+
+
+def dtype_name(vol):
+    return {np.dtype(np.uint8): "u8", np.dtype(np.uint16): "u16", np.dtype(np.float16): "f16",
+            np.dtype(np.float32): "f32"}[vol.dtype]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    import torch
+
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(w, seconds):
+    """Time the FP64 oracle on a band of image rows (bounded to about `seconds`)."""
+    import oracle
+
+    ov = oracle.OracleVolume(w["volume"], w["value_max"])
+    pr = oracle.make_params(step=w["step"], grad=w["grad"])
+    cam = w["camera"]
+    H = cam["height"]
+    mid = H // 2
+    rows = 2
+    t0 = time.perf_counter()
+    _, _, total = oracle.render(ov, w["tf"], cam, pr, rows=(mid, mid + rows))
+    dt = time.perf_counter() - t0
+    # grow the band so that the measured run lasts about `seconds`
+    target = max(2, min(H // 2, int(rows * seconds / max(dt, 1e-3))))
+    r0 = max(0, mid - target // 2)
+    t0 = time.perf_counter()
+    _, _, total = oracle.render(ov, w["tf"], cam, pr, rows=(r0, r0 + target))
+    dt = time.perf_counter() - t0
+    return {"samples": int(total), "seconds": dt, "rows": [r0, r0 + target],
+            "cores": oracle.num_threads()}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    vals = []
+    samples = 0
+    secs = 0.0
+    per_step = max(3.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(w, per_step)
+        if i >= args.warmup:
+            vals.append(r["samples"] / r["seconds"] / 1e9)
+            samples += r["samples"]
+            secs += r["seconds"]
+    value = samples / secs / 1e9
+    cam = w["camera"]
+    line = {
+        "impl": "reference", "metric": "Gsamples/s", "value": value, "unit": "Gsamples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "image": f"{cam['width']}x{cam['height']}",
+                   "grad": w["grad"], "step": w["step"]},
+        "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": r["cores"],
+                         "kind": "oracle",
+                         "sample": f"rows {r['rows'][0]}-{r['rows'][1]} of the "
+                                   f"{cam['width']}x{cam['height']} frame per step"},
+        "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------ GPU leg
+def run_ours(args):
+    import torch
+
+    from paper_1609_01317_gb300 import Renderer, build, vr
+
+    rank, world, local = dist_setup(args)
+    build.build()
+    w = workload(args.workload)
+    vol = w["volume"]
+    nz, ny, nx = vol.shape
+    dt = dtype_name(vol)
+    cam = w["camera"]
+    H, W = cam["height"], cam["width"]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream or None
+    vol_dev = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
+    tf_dev = torch.from_numpy(w["tf"]).cuda()
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    R = Renderer(local)
+    ctx = R.ctx
+    params = vr.make_params(step=w["step"], grad=w["grad"], skip_empty=w["skip_empty"])
+    cam_s = vr.make_camera(cam)
+
+    def step(p=params):
+        vr.vr_upload_volume(ctx, vol_dev, dt, nx, ny, nz, w["value_max"], sh)
+        vr.vr_set_transfer_function(ctx, tf_dev, tf_dev.shape[0], sh)
+        vr.vr_set_camera(ctx, cam_s)
+        vr.vr_render(ctx, p, out, sh)
+
+    # sample counts (untimed): the numerator of the metric
+    pst = vr.make_params(step=w["step"], grad=w["grad"], skip_empty=w["skip_empty"],
+                         collect_stats=True)
+    step(pst)
+    stats = vr.vr_read_stats(ctx, sh)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    barrier(world)
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(K):
+            flush.fill_(float(i))  # evict the L2 between steps (outside the timed events)
+            ev[i][0].record(stream)
+            vr.vr_upload_volume(ctx, vol_dev, dt, nx, ny, nz, w["value_max"], sh)
+            vr.vr_set_transfer_function(ctx, tf_dev, tf_dev.shape[0], sh)
+            vr.vr_set_camera(ctx, cam_s)
+            ev[i][1].record(stream)
+            vr.vr_render(ctx, params, out, sh)
+            ev[i][2].record(stream)
+        barrier(world)
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(K)]
+    march_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    samples = stats["samples_plain"]
+    value = sum_over_ranks(samples * K, world) / (total_ms / 1e3) / 1e9
+    ms_per_step = total_ms / K
+    march_avg = statistics.mean(march_ms)
+
+    # roofline of the dominant kernel (the fused march)
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    flops = stats["samples_visited"] * FLOPS_VISIT + stats["samples_shaded"] * FLOPS_SHADE[w["grad"]]
+    achieved = flops / (march_avg / 1e3) / 1e12
+    bpv = {"u8": 1, "u16": 2, "f16": 2, "f32": 4}[dt]
+    hbm_bytes = (nx + 3) * (ny + 3) * (nz + 3) * bpv + H * W * 16
+    hbm_achieved = hbm_bytes / (march_avg / 1e3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": achieved / alu_peak, "traffic": None,
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": float(pk["hbm_gbs"]),
+                "unit": "GB/s", "frac": hbm_achieved / float(pk["hbm_gbs"]),
+                "peak_source": f"{pk_kind} copy bandwidth"}
+
+    line = {
+        "metric": "Gsamples/s", "value": value, "unit": "Gsamples/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "volume": f"{nx}x{ny}x{nz} {dt}",
+                   "image": f"{W}x{H}", "grad": w["grad"], "step": w["step"],
+                   "skip_empty": w["skip_empty"], "ert": 0.99,
+                   "l2": "flushed between steps (256 MiB write); volume 189 MB > L2",
+                   "parallelism": f"replicas{world}"},
+        "frames_per_s": 1000.0 / ms_per_step,
+        "march_ms": march_avg,
+        "samples_per_frame": samples,
+        "samples_visited": stats["samples_visited"],
+        "samples_shaded": stats["samples_shaded"],
+        "rays_hit": stats["rays_hit"],
+        "roofline": roof,
+        "roofline_hbm": roof_hbm,
+        "gpu_launches": 5 * K,
+        "wall_s": t_wall,
+    }
+    line["clocks"] = clk.summary()
+
+    if not args.no_extras and world == 1:
+        # end to end through the C ABI with host buffers: H2D of the volume and TF, D2H of
+        # the image, every step
+        host_vol = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).pin_memory()
+        host_tf = torch.from_numpy(w["tf"]).pin_memory()
+        host_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            vr.vr_upload_volume(ctx, host_vol, dt, nx, ny, nz, w["value_max"], sh)
+            vr.vr_set_transfer_function(ctx, host_tf, host_tf.shape[0], sh)
+            vr.vr_set_camera(ctx, cam_s)
+            vr.vr_render(ctx, params, host_out, sh)
+        torch.cuda.synchronize()
+        ke = max(3, min(K, 10))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            vr.vr_upload_volume(ctx, host_vol, dt, nx, ny, nz, w["value_max"], sh)
+            vr.vr_set_transfer_function(ctx, host_tf, host_tf.shape[0], sh)
+            vr.vr_set_camera(ctx, cam_s)
+            vr.vr_render(ctx, params, host_out, sh)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / ke
+        ok = torch.equal(host_out, out.cpu())
+        line["e2e"] = {"value": samples / e2e_s / 1e9, "unit": "Gsamples/s",
+                       "h2d_bytes_per_step": int(vol.nbytes + w["tf"].nbytes),
+                       "d2h_bytes_per_step": int(H * W * 16), "ms_per_step": e2e_s * 1e3,
+                       "matches_device_result": bool(ok)}
+        # CPU baseline: the FP64 oracle on a bounded sample of the same workload
+        cb = oracle_sample(w, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": cb["samples"] / cb["seconds"] / 1e9,
+                                "unit": "Gsamples/s", "cores": cb["cores"], "kind": "oracle",
+                                "sample": f"image rows {cb['rows'][0]}-{cb['rows'][1]} "
+                                          f"({cb['samples']} samples, {cb['seconds']:.1f} s)"}
+    else:
+        line["e2e"] = None
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    R.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * vr.h -- C ABI of libvr, a direct volume ray caster for NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one described in N. Kopal, "Volume Raycasting mit OpenCL" (2011,
+ * arXiv:1609.01317), §3.10 "Gesamtaufbau eines Raycasters": for every pixel cast a ray,
+ * intersect it with the bounding box (§3.3, §3.6), sample the volume at regular spacing
+ * with trilinear interpolation (§3.4, Eq. 2), estimate a gradient with the central
+ * difference, Sobel3D or Zucker-Hummel operator (§3.5, Eq. 3, Eq. 4), look up colour and
+ * opacity in a transfer-function table (§3.7), shade with a point light (§3.8, Listing 3,
+ * extended to Phong) and composite with the transparency formula (§3.9, Eq. 6) front to
+ * back with early ray termination.  Empty space is skipped with per-brick min/max tables
+ * (§5.3 "Empty-Space-Skipping", §5.4 "Octree").  A hand-written adjoint makes the image
+ * differentiable with respect to voxel values and transfer-function entries.
+ *
+ * General conventions (apply to every entry point unless stated otherwise):
+ *   - Every call returns a vr_status.  Argument errors are detected before any work is
+ *     queued and leave the context unchanged (VR_ERR_INVALID_ARG, VR_ERR_UNSUPPORTED,
+ *     VR_ERR_STATE).  CUDA errors, including asynchronous ones from earlier launches, are
+ *     reported as VR_ERR_CUDA by the next call that checks.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work is queued
+ *     on it and is asynchronous unless the call says it synchronises.
+ *   - Caller buffers are never freed or retained past the call; buffers the library needs
+ *     (padded volume, brick tables, transfer function, staging, adjoint scratch) come from
+ *     the allocator given to vr_create and are released by vr_destroy.
+ *   - Volumes are dense x-fastest arrays: voxel (x, y, z) is element x + nx*(y + ny*z)
+ *     and sits at world point (x, y, z) (unit spacing, §2.1 Eq. 1).
+ *   - Images are H x W x 4 float32 RGBA, row-major, row 0 at the top; RGB is
+ *     premultiplied over black and A = 1 - transmittance.
+ *   - A context may be used from one host thread at a time.
+ */
+#ifndef VR_H
+#define VR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vr_ctx vr_ctx;
+
+typedef enum {
+    VR_OK = 0,
+    VR_ERR_INVALID_ARG = 1,   /* a pointer, size or parameter is out of its range      */
+    VR_ERR_OUT_OF_MEMORY = 2, /* the allocator returned NULL                           */
+    VR_ERR_CUDA = 3,          /* a CUDA call failed (text via vr_last_cuda_error)      */
+    VR_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement          */
+    VR_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                    */
+    VR_ERR_STATE = 6          /* call order violated (no volume / no TF / no camera,   */
+                              /* or checkpoints that do not match the current state)   */
+} vr_status;
+
+/* Voxel storage types (§3.2: CT data are 12-bit values in 16-bit shorts). */
+typedef enum { VR_U8 = 0, VR_U16 = 1, VR_F16 = 2, VR_F32 = 3 } vr_dtype;
+
+/* Gradient operators of §3.5. */
+typedef enum {
+    VR_GRAD_CENTRAL = 0,      /* Eq. 3, 6 taps                                          */
+    VR_GRAD_SOBEL3D = 1,      /* Eq. 4, weights 1,3,6 per plane, 54 taps                */
+    VR_GRAD_ZUCKER_HUMMEL = 2 /* 54 taps, weight of neighbour (+-1,b,c) = +-1/sqrt(1+b^2+c^2) */
+} vr_grad;
+
+/* Pinhole or orthographic camera (§3.3: one ray through every pixel).
+ *   fwd = normalize(target - eye), right = normalize(fwd x up), up' = right x fwd.
+ *   Pixel (px, py) has screen coordinates u = (2(px+1/2)/W - 1) * ax and
+ *   v = (1 - 2(py+1/2)/H) * ay, with ay = tan(fov_y/2) (perspective) or ortho_height/2
+ *   (orthographic) and ax = ay * W / H.
+ *   Perspective: origin eye, direction normalize(fwd + u right + v up').
+ *   Orthographic: origin eye + u right + v up', direction fwd.
+ * The ray setup is evaluated in FP32 with every operation rounded separately, so the
+ * integer sample count of each ray is reproducible on any IEEE-754 machine. */
+typedef struct {
+    float eye[3], target[3], up[3];
+    int ortho;          /* 0 = perspective, 1 = orthographic                          */
+    float fov_y_deg;    /* perspective vertical field of view, in (0, 180)            */
+    float ortho_height; /* orthographic image height in world units, > 0              */
+    int width, height;  /* image size in pixels, 1 .. 16384 each                      */
+} vr_camera;
+
+/* Per-render parameters. */
+typedef struct {
+    float step;          /* sample spacing along the unit ray direction, > 0 (§3.3)     */
+    int grad;            /* vr_grad                                                     */
+    float ka, kd, ks;    /* Phong ambient / diffuse / specular coefficients             */
+    float shininess;     /* Phong exponent, >= 0                                        */
+    float light[3];      /* point-light position (§3.8), used when headlight == 0       */
+    int headlight;       /* 1: the light sits at the eye                                */
+    float ert_threshold; /* stop a ray once 1 - T >= this, in (0, 1]; > 1 never stops   */
+    int skip_empty;      /* 1: skip bricks whose opacity is zero for the current TF    */
+    float clip_lo[3];    /* clip box (§3.6), intersected with [0, n-1]^3               */
+    float clip_hi[3];
+    int collect_stats;   /* 1: count rays and samples (read with vr_read_stats)         */
+} vr_render_params;
+
+/* Sample counters of the most recent render with collect_stats = 1. */
+typedef struct {
+    unsigned long long rays_hit;        /* rays with at least one sample               */
+    unsigned long long samples_plain;   /* samples the plain method marches: every     */
+                                        /* t_k up to early termination, skipped or not */
+    unsigned long long samples_visited; /* samples actually interpolated               */
+    unsigned long long samples_shaded;  /* samples with opacity != 0 (gradient+Phong)  */
+} vr_stats;
+
+/* Device allocator callback pair: alloc returns device memory aligned to 256 bytes or
+ * NULL; free releases it.  Both may be NULL to use cudaMalloc / cudaFree. */
+typedef void *(*vr_alloc_fn)(size_t bytes, void *user);
+typedef void (*vr_free_fn)(void *ptr, void *user);
+
+/* Create a context on CUDA device `device`.  *out receives the handle (NULL on error).
+ * Errors: INVALID_ARG (out NULL, only one of alloc/free given), CUDA (no such device). */
+vr_status vr_create(vr_ctx **out, int device, vr_alloc_fn alloc, vr_free_fn free_fn,
+                    void *user);
+
+/* Release every buffer of the context (after synchronising the device).  NULL is a no-op. */
+void vr_destroy(vr_ctx *ctx);
+
+/* Upload a volume (§3.1, §3.2: the host loads the slices and copies them to the GPU).
+ * `voxels` is a dense nx*ny*nz array of `dtype` in host or device memory (detected);
+ * it is only read during the call's stream work (host memory: before the call returns).
+ * value_max maps raw values to [0, 1]: s = raw / value_max (255 for u8, 4095 for
+ * 12-bit u16, 1 for f16/f32).  The library stores a copy with a clamp-to-edge border and
+ * per-brick (8^3) min/max tables; if a transfer function is set, brick visibility is
+ * recomputed.  Errors: INVALID_ARG (NULL, a size < 1, nx*ny*nz > 2^31, value_max <= 0),
+ * UNSUPPORTED (dtype), OUT_OF_MEMORY, CUDA. */
+vr_status vr_upload_volume(vr_ctx *ctx, const void *voxels, vr_dtype dtype, int nx, int ny,
+                           int nz, float value_max, void *stream);
+
+/* Set the transfer function (§3.7 colour lookup table): n RGBA float32 entries in host or
+ * device memory, entry i covering s = i / (n - 1), read with linear interpolation between
+ * entries.  Values are used as given (no clamping of alpha).  Recomputes the per-brick
+ * visibility flags when a volume is present.  Errors: INVALID_ARG (NULL, n < 2,
+ * n > 65536), OUT_OF_MEMORY, CUDA. */
+vr_status vr_set_transfer_function(vr_ctx *ctx, const float *rgba, int n, void *stream);
+
+/* Set the camera used by the following renders (host struct, copied).
+ * Errors: INVALID_ARG (NULL, size out of range, fov out of (0,180), ortho_height <= 0,
+ * eye == target, up parallel to the view direction, non-finite values). */
+vr_status vr_set_camera(vr_ctx *ctx, const vr_camera *cam);
+
+/* Render the current volume / transfer function / camera into out_rgba (H x W x 4 float32,
+ * host or device memory, detected; host output is copied back on `stream` and is valid
+ * once the stream is synchronised).  Errors: INVALID_ARG (NULL, step <= 0, ert_threshold
+ * <= 0, shininess < 0, grad out of range, non-finite parameters), STATE (no volume, TF or
+ * camera), OUT_OF_MEMORY, CUDA.  An empty clip box gives a black transparent image. */
+vr_status vr_render(vr_ctx *ctx, const vr_render_params *params, float *out_rgba, void *stream);
+
+/* Bytes of the checkpoint buffer vr_render_forward_train needs for the current camera,
+ * volume and `params` (per-ray end index plus transmittance every 32 samples). */
+vr_status vr_checkpoint_bytes(vr_ctx *ctx, const vr_render_params *params, size_t *bytes);
+
+/* vr_render that also records, in the caller-owned device buffer `checkpoints` (at least
+ * vr_checkpoint_bytes bytes, 256-byte aligned), what vr_render_backward needs: each ray's
+ * end index and its transmittance before every 32nd sample.  out_rgba must be device
+ * memory.  Errors as vr_render, plus INVALID_ARG for a short or unaligned buffer. */
+vr_status vr_render_forward_train(vr_ctx *ctx, const vr_render_params *params,
+                                  float *out_rgba, void *checkpoints, size_t checkpoint_bytes,
+                                  void *stream);
+
+/* Adjoint of vr_render_forward_train (reverse-mode differentiation of Eq. 6 through the
+ * shading, normal, gradient operator, transfer function and trilinear interpolation).
+ * grad_rgba: dL/dRGBA, H x W x 4 float32 device.  Accumulates (+=) dL/d(raw voxel) into
+ * grad_volume (device float32, nx*ny*nz, x fastest) and dL/d(TF entry) into grad_tf
+ * (device float32, n x 4); either may be NULL to skip it.  The rays are walked back to
+ * front segment by segment, each segment recomputed from its stored transmittance.
+ * Errors: INVALID_ARG, STATE (checkpoints not written by vr_render_forward_train for the
+ * current volume, transfer function, camera and params), OUT_OF_MEMORY, CUDA. */
+vr_status vr_render_backward(vr_ctx *ctx, const vr_render_params *params,
+                             const void *checkpoints, const float *grad_rgba,
+                             float *grad_volume, float *grad_tf, void *stream);
+
+/* Copy the counters of the last render with collect_stats = 1 into *out.  Synchronises
+ * `stream`.  Errors: INVALID_ARG, STATE (no such render), CUDA. */
+vr_status vr_read_stats(vr_ctx *ctx, vr_stats *out, void *stream);
+
+/* Short English text of a status code (static storage). */
+const char *vr_status_string(vr_status status);
+
+/* Text of the last CUDA error seen by this thread (static storage, "" if none). */
+const char *vr_last_cuda_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int vr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VR_H */

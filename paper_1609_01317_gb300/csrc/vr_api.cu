@@ -1,0 +1,559 @@
+// vr_api.cu -- the C ABI of libvr (argument validation, state, memory, launches).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "vr_internal.h"
+
+namespace vr {
+
+static thread_local char g_cuda_err[256] = "";
+
+vr_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return VR_OK;
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e),
+                cudaGetErrorString(e));
+  return VR_ERR_CUDA;
+}
+
+vr_status ctx_alloc(vr_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (ctx->alloc) {
+    *p = ctx->alloc(bytes, ctx->user);
+    return *p ? VR_OK : VR_ERR_OUT_OF_MEMORY;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    *p = nullptr;
+    return VR_ERR_OUT_OF_MEMORY;
+  }
+  return cuda_status(e);
+}
+
+void ctx_free(vr_ctx* ctx, void* p) {
+  if (!p) return;
+  if (ctx->free_fn) ctx->free_fn(p, ctx->user);
+  else cudaFree(p);
+}
+
+// Grow-only buffer: reallocates (without preserving contents) when `bytes` exceeds *cap.
+vr_status ensure(vr_ctx* ctx, void** p, size_t* cap, size_t bytes) {
+  if (*p && *cap >= bytes) return VR_OK;
+  if (*p) {
+    cudaDeviceSynchronize();  // the old buffer may still be read by queued work
+    ctx_free(ctx, *p);
+    *p = nullptr;
+    *cap = 0;
+  }
+  const vr_status st = ctx_alloc(ctx, p, bytes);
+  if (st == VR_OK) *cap = bytes;
+  return st;
+}
+
+// Switches to the context's device for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; }
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+static bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static bool finite3(const float v[3]) {
+  return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+static int dtype_bytes(vr_dtype t) {
+  switch (t) {
+    case VR_U8: return 1;
+    case VR_U16: return 2;
+    case VR_F16: return 2;
+    case VR_F32: return 4;
+  }
+  return 0;
+}
+
+VolDev vol_dev(const vr_ctx* ctx) {
+  VolDev V;
+  V.data = ctx->vol;
+  for (int a = 0; a < 3; ++a) {
+    V.n[a] = ctx->n[a];
+    V.nb[a] = ctx->nb[a];
+  }
+  V.px = ctx->px;
+  V.py = ctx->py;
+  V.pxy = ctx->px * ctx->py;
+  V.value_max = ctx->value_max;
+  V.vis = ctx->brick_vis;
+  return V;
+}
+
+TfDev tf_dev(const vr_ctx* ctx) {
+  TfDev t;
+  t.tf = ctx->tf;
+  t.n = ctx->ntf;
+  t.scale = (float)(ctx->ntf - 1) / ctx->value_max;
+  return t;
+}
+
+RenderDev render_dev(const vr_ctx* ctx, const vr_render_params* p) {
+  RenderDev r;
+  r.step = p->step;
+  r.ert = p->ert_threshold;
+  r.skip = p->skip_empty ? 1 : 0;
+  for (int a = 0; a < 3; ++a) {
+    const float vhi = (float)(ctx->n[a] - 1);
+    r.lo[a] = p->clip_lo[a] > 0.0f ? p->clip_lo[a] : 0.0f;
+    r.hi[a] = p->clip_hi[a] < vhi ? p->clip_hi[a] : vhi;
+  }
+  r.gscale = op_scale(p->grad) / ctx->value_max;
+  r.sh.ka = p->ka;
+  r.sh.kd = p->kd;
+  r.sh.ks = p->ks;
+  r.sh.shininess = p->shininess;
+  for (int a = 0; a < 3; ++a) r.sh.light[a] = p->light[a];
+  r.sh.headlight = p->headlight ? 1 : 0;
+  return r;
+}
+
+// Upper bound of the per-ray sample count K for the current box and step.
+int max_samples(const vr_ctx* ctx, const vr_render_params* p) {
+  const RenderDev r = render_dev(ctx, p);
+  double d2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double e = (double)r.hi[a] - (double)r.lo[a];
+    if (e > 0) d2 += e * e;
+  }
+  const double k = std::floor(std::sqrt(d2) / (double)p->step + 0.5) + 2.0;
+  return k > 1.5e9 ? 1500000000 : (int)k;
+}
+
+// FP32 camera basis with every operation rounded on its own (this file is compiled with
+// -ffp-contract=off for the host): fwd, right, up' and the screen half-extents.
+static bool camera_basis(const vr_camera* c, CamDev* b) {
+  float f[3], r[3], u[3];
+  for (int a = 0; a < 3; ++a) f[a] = c->target[a] - c->eye[a];
+  float l = f[0] * f[0];
+  l = l + f[1] * f[1];
+  l = l + f[2] * f[2];
+  l = std::sqrt(l);
+  if (!(l > 0.0f) || !std::isfinite(l)) return false;
+  for (int a = 0; a < 3; ++a) f[a] = f[a] / l;
+  r[0] = f[1] * c->up[2] - f[2] * c->up[1];
+  r[1] = f[2] * c->up[0] - f[0] * c->up[2];
+  r[2] = f[0] * c->up[1] - f[1] * c->up[0];
+  l = r[0] * r[0];
+  l = l + r[1] * r[1];
+  l = l + r[2] * r[2];
+  l = std::sqrt(l);
+  if (!(l > 0.0f) || !std::isfinite(l)) return false;
+  for (int a = 0; a < 3; ++a) r[a] = r[a] / l;
+  u[0] = r[1] * f[2] - r[2] * f[1];
+  u[1] = r[2] * f[0] - r[0] * f[2];
+  u[2] = r[0] * f[1] - r[1] * f[0];
+  double half;
+  if (c->ortho) half = (double)(c->ortho_height / 2.0f);
+  else half = std::tan(((double)c->fov_y_deg * M_PI) / 360.0);
+  for (int a = 0; a < 3; ++a) {
+    b->eye[a] = c->eye[a];
+    b->fwd[a] = f[a];
+    b->right[a] = r[a];
+    b->upv[a] = u[a];
+  }
+  b->ay = (float)half;
+  b->ax = (float)((half * (double)c->width) / (double)c->height);
+  b->ortho = c->ortho ? 1 : 0;
+  b->width = c->width;
+  b->height = c->height;
+  return true;
+}
+
+static vr_status check_params(const vr_render_params* p) {
+  if (!p) return VR_ERR_INVALID_ARG;
+  if (!(p->step > 0.0f) || !std::isfinite(p->step)) return VR_ERR_INVALID_ARG;
+  if (p->grad < VR_GRAD_CENTRAL || p->grad > VR_GRAD_ZUCKER_HUMMEL) return VR_ERR_INVALID_ARG;
+  if (!(p->ert_threshold > 0.0f) || std::isnan(p->ert_threshold)) return VR_ERR_INVALID_ARG;
+  if (!(p->shininess >= 0.0f) || !std::isfinite(p->shininess)) return VR_ERR_INVALID_ARG;
+  if (!std::isfinite(p->ka) || !std::isfinite(p->kd) || !std::isfinite(p->ks))
+    return VR_ERR_INVALID_ARG;
+  if (!finite3(p->light)) return VR_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (std::isnan(p->clip_lo[a]) || std::isnan(p->clip_hi[a])) return VR_ERR_INVALID_ARG;
+  return VR_OK;
+}
+
+static vr_status refresh_visibility(vr_ctx* ctx, cudaStream_t s) {
+  if (!ctx->has_volume || !ctx->has_tf) return VR_OK;
+  const float scale = (float)(ctx->ntf - 1) / ctx->value_max;
+  return cuda_status(
+      launch_brick_visibility(ctx->brick_minmax, ctx->nb, ctx->tf_prefix, ctx->ntf, scale,
+                              ctx->brick_vis, s));
+}
+
+static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* out,
+                               int* ck_kend, float* ck_T, int nslots, cudaStream_t s) {
+  MarchLaunch L;
+  L.V = vol_dev(ctx);
+  L.tf = tf_dev(ctx);
+  L.cam = ctx->camdev;
+  L.r = render_dev(ctx, p);
+  L.dtype = (int)ctx->dtype;
+  L.op = p->grad;
+  L.out = reinterpret_cast<float4*>(out);
+  L.stats = nullptr;
+  L.ck_kend = ck_kend;
+  L.ck_T = ck_T;
+  L.nslots = nslots;
+  if (p->collect_stats) {
+    vr_status st = cuda_status(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
+    if (st != VR_OK) return st;
+    L.stats = ctx->stats;
+  }
+  const vr_status st = cuda_status(launch_march(L, s));
+  if (st == VR_OK) ctx->stats_valid = ctx->stats_valid || p->collect_stats;
+  return st;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static void ckpt_layout(vr_ctx* ctx, const vr_render_params* p, int* nrays, int* nslots,
+                        size_t* bytes) {
+  *nrays = ctx->cam.width * ctx->cam.height;
+  const int kmax = max_samples(ctx, p);
+  *nslots = kmax > 1 ? (kmax - 1) / kCkptStride : 0;
+  *bytes = align256((size_t)*nrays * 4) + (size_t)*nrays * 4 * (size_t)*nslots;
+}
+
+}  // namespace vr
+
+using namespace vr;
+
+extern "C" {
+
+vr_status vr_create(vr_ctx** out, int device, vr_alloc_fn alloc, vr_free_fn free_fn, void* user) {
+  if (!out) return VR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((alloc == nullptr) != (free_fn == nullptr)) return VR_ERR_INVALID_ARG;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (device < 0 || device >= count) return VR_ERR_INVALID_ARG;
+  vr_ctx* ctx = new (std::nothrow) vr_ctx();
+  if (!ctx) return VR_ERR_OUT_OF_MEMORY;
+  ctx->device = device;
+  ctx->alloc = alloc;
+  ctx->free_fn = free_fn;
+  ctx->user = user;
+  DeviceGuard g(device);
+  if (!g.ok) {
+    delete ctx;
+    return cuda_status(cudaGetLastError());
+  }
+  void* st = nullptr;
+  const vr_status s = ctx_alloc(ctx, &st, 4 * sizeof(unsigned long long));
+  if (s != VR_OK) {
+    delete ctx;
+    return s;
+  }
+  ctx->stats = static_cast<unsigned long long*>(st);
+  *out = ctx;
+  return VR_OK;
+}
+
+void vr_destroy(vr_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  ctx_free(ctx, ctx->vol);
+  ctx_free(ctx, ctx->brick_minmax);
+  ctx_free(ctx, ctx->upload_staging);
+  ctx_free(ctx, ctx->tf);
+  ctx_free(ctx, ctx->stats);
+  ctx_free(ctx, ctx->out_staging);
+  ctx_free(ctx, ctx->adj);
+  delete ctx;
+}
+
+vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int nx, int ny,
+                           int nz, float value_max, void* stream) {
+  if (!ctx || !voxels) return VR_ERR_INVALID_ARG;
+  if (nx < 1 || ny < 1 || nz < 1) return VR_ERR_INVALID_ARG;
+  if (!(value_max > 0.0f) || !std::isfinite(value_max)) return VR_ERR_INVALID_ARG;
+  const int eb = dtype_bytes(dtype);
+  if (eb == 0) return VR_ERR_UNSUPPORTED;
+  const long long nvox = (long long)nx * ny * nz;
+  // x pitch: a multiple of 16 elements and at least nx + 8, so that the vector row loads
+  // of the brick footprints (which start at padded x = 8 bx) stay inside each row
+  const long long px = ((long long)nx + 8 + 15) / 16 * 16;
+  const long long py = ny + kPadLo + kPadHi, pz = nz + kPadLo + kPadHi;
+  if (nvox > 2147483647LL || px * py * pz > 2147483647LL) return VR_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const void* src = voxels;
+  vr_status st;
+  if (!is_device_pointer(voxels)) {
+    st = ensure(ctx, &ctx->upload_staging, &ctx->upload_cap, (size_t)nvox * eb);
+    if (st != VR_OK) return st;
+    st = cuda_status(cudaMemcpyAsync(ctx->upload_staging, voxels, (size_t)nvox * eb,
+                                     cudaMemcpyHostToDevice, s));
+    if (st != VR_OK) return st;
+    src = ctx->upload_staging;
+  }
+  st = ensure(ctx, &ctx->vol, &ctx->vol_cap, (size_t)(px * py * pz) * eb);
+  if (st != VR_OK) return st;
+  const int nb[3] = {(nx + kBrick - 1) / kBrick, (ny + kBrick - 1) / kBrick,
+                     (nz + kBrick - 1) / kBrick};
+  const size_t nbricks = (size_t)nb[0] * nb[1] * nb[2];
+  void* bt = ctx->brick_minmax;
+  st = ensure(ctx, &bt, &ctx->brick_cap, align256(nbricks * sizeof(float2)) + nbricks);
+  if (st != VR_OK) return st;
+  ctx->brick_minmax = static_cast<float2*>(bt);
+  ctx->brick_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) +
+                                              align256(nbricks * sizeof(float2)));
+  ctx->dtype = dtype;
+  ctx->n[0] = nx; ctx->n[1] = ny; ctx->n[2] = nz;
+  ctx->px = (int)px; ctx->py = (int)py; ctx->pz = (int)pz;
+  for (int a = 0; a < 3; ++a) ctx->nb[a] = nb[a];
+  ctx->value_max = value_max;
+  st = cuda_status(launch_pad_volume(src, (int)dtype, ctx->n, ctx->vol, ctx->px, ctx->py,
+                                     ctx->pz, s));
+  if (st != VR_OK) return st;
+  st = cuda_status(launch_brick_minmax(vol_dev(ctx), (int)dtype, ctx->brick_minmax, s));
+  if (st != VR_OK) return st;
+  if (!ctx->has_tf) {
+    // no transfer function yet: everything visible until one is set
+    st = cuda_status(cudaMemsetAsync(ctx->brick_vis, 1, nbricks, s));
+    if (st != VR_OK) return st;
+  }
+  ctx->has_volume = true;
+  ++ctx->vol_gen;
+  st = refresh_visibility(ctx, s);
+  if (st != VR_OK) return st;
+  if (!is_device_pointer(voxels)) {
+    // the staging copy is read by the padding kernel: keep the host buffer's contract
+    // ("read before the call returns") by waiting for the H2D copy.
+    st = cuda_status(cudaStreamSynchronize(s));
+  }
+  return st;
+}
+
+vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, void* stream) {
+  if (!ctx || !rgba || n < 2 || n > 65536) return VR_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* buf = ctx->tf;
+  const size_t tfb = align256((size_t)n * sizeof(float4));
+  vr_status st = ensure(ctx, &buf, &ctx->tf_cap, tfb + (size_t)(n + 1) * sizeof(int));
+  if (st != VR_OK) return st;
+  ctx->tf = static_cast<float4*>(buf);
+  ctx->tf_prefix = reinterpret_cast<int*>(static_cast<char*>(buf) + tfb);
+  const bool dev = is_device_pointer(rgba);
+  st = cuda_status(cudaMemcpyAsync(ctx->tf, rgba, (size_t)n * sizeof(float4),
+                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (st != VR_OK) return st;
+  st = cuda_status(launch_tf_prefix(ctx->tf, n, ctx->tf_prefix, s));
+  if (st != VR_OK) return st;
+  ctx->ntf = n;
+  ctx->has_tf = true;
+  ++ctx->tf_gen;
+  st = refresh_visibility(ctx, s);
+  if (st == VR_OK && !dev) st = cuda_status(cudaStreamSynchronize(s));
+  return st;
+}
+
+vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cam) {
+  if (!ctx || !cam) return VR_ERR_INVALID_ARG;
+  if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+    return VR_ERR_INVALID_ARG;
+  if (!finite3(cam->eye) || !finite3(cam->target) || !finite3(cam->up)) return VR_ERR_INVALID_ARG;
+  if (cam->ortho) {
+    if (!(cam->ortho_height > 0.0f) || !std::isfinite(cam->ortho_height)) return VR_ERR_INVALID_ARG;
+  } else {
+    if (!(cam->fov_y_deg > 0.0f && cam->fov_y_deg < 180.0f)) return VR_ERR_INVALID_ARG;
+  }
+  CamDev b;
+  if (!camera_basis(cam, &b)) return VR_ERR_INVALID_ARG;
+  ctx->cam = *cam;
+  ctx->camdev = b;
+  ctx->has_camera = true;
+  return VR_OK;
+}
+
+vr_status vr_render(vr_ctx* ctx, const vr_render_params* params, float* out_rgba, void* stream) {
+  if (!ctx || !out_rgba) return VR_ERR_INVALID_ARG;
+  vr_status st = check_params(params);
+  if (st != VR_OK) return st;
+  if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->cam.width * ctx->cam.height * sizeof(float4);
+  float* dst = out_rgba;
+  const bool host_out = !is_device_pointer(out_rgba);
+  if (host_out) {
+    st = ensure(ctx, &ctx->out_staging, &ctx->out_cap, bytes);
+    if (st != VR_OK) return st;
+    dst = static_cast<float*>(ctx->out_staging);
+  }
+  st = render_common(ctx, params, dst, nullptr, nullptr, 0, s);
+  if (st != VR_OK) return st;
+  if (host_out)
+    st = cuda_status(cudaMemcpyAsync(out_rgba, dst, bytes, cudaMemcpyDeviceToHost, s));
+  return st;
+}
+
+vr_status vr_checkpoint_bytes(vr_ctx* ctx, const vr_render_params* params, size_t* bytes) {
+  if (!ctx || !bytes) return VR_ERR_INVALID_ARG;
+  vr_status st = check_params(params);
+  if (st != VR_OK) return st;
+  if (!ctx->has_volume || !ctx->has_camera) return VR_ERR_STATE;
+  int nrays, nslots;
+  ckpt_layout(ctx, params, &nrays, &nslots, bytes);
+  return VR_OK;
+}
+
+vr_status vr_render_forward_train(vr_ctx* ctx, const vr_render_params* params, float* out_rgba,
+                                  void* checkpoints, size_t checkpoint_bytes, void* stream) {
+  if (!ctx || !out_rgba || !checkpoints) return VR_ERR_INVALID_ARG;
+  vr_status st = check_params(params);
+  if (st != VR_OK) return st;
+  if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
+  if (((uintptr_t)checkpoints & 255) != 0) return VR_ERR_INVALID_ARG;
+  int nrays, nslots;
+  size_t need;
+  ckpt_layout(ctx, params, &nrays, &nslots, &need);
+  if (checkpoint_bytes < need) return VR_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  if (!is_device_pointer(out_rgba) || !is_device_pointer(checkpoints)) return VR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* kend = static_cast<int*>(checkpoints);
+  float* T = reinterpret_cast<float*>(static_cast<char*>(checkpoints) + align256((size_t)nrays * 4));
+  st = render_common(ctx, params, out_rgba, kend, T, nslots, s);
+  if (st != VR_OK) return st;
+  // remember what was recorded (replace an older record of the same buffer)
+  int slot = -1;
+  for (int i = 0; i < kMaxCkptRecords; ++i)
+    if (ctx->ckpt[i].ptr == checkpoints) slot = i;
+  if (slot < 0) {
+    slot = ctx->ckpt_next;
+    ctx->ckpt_next = (ctx->ckpt_next + 1) % kMaxCkptRecords;
+  }
+  CkptRecord& r = ctx->ckpt[slot];
+  r.ptr = checkpoints;
+  r.bytes = checkpoint_bytes;
+  r.cam = ctx->cam;
+  r.params = *params;
+  r.vol_gen = ctx->vol_gen;
+  r.tf_gen = ctx->tf_gen;
+  r.nrays = nrays;
+  r.nslots = nslots;
+  return VR_OK;
+}
+
+vr_status vr_render_backward(vr_ctx* ctx, const vr_render_params* params, const void* checkpoints,
+                             const float* grad_rgba, float* grad_volume, float* grad_tf,
+                             void* stream) {
+  if (!ctx || !checkpoints || !grad_rgba) return VR_ERR_INVALID_ARG;
+  vr_status st = check_params(params);
+  if (st != VR_OK) return st;
+  if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
+  const CkptRecord* rec = nullptr;
+  for (int i = 0; i < kMaxCkptRecords; ++i)
+    if (ctx->ckpt[i].ptr == checkpoints) rec = &ctx->ckpt[i];
+  if (!rec) return VR_ERR_STATE;
+  if (rec->vol_gen != ctx->vol_gen || rec->tf_gen != ctx->tf_gen) return VR_ERR_STATE;
+  if (std::memcmp(&rec->cam, &ctx->cam, sizeof(vr_camera)) != 0) return VR_ERR_STATE;
+  vr_render_params a = rec->params, b = *params;
+  a.collect_stats = b.collect_stats = 0;
+  if (std::memcmp(&a, &b, sizeof(vr_render_params)) != 0) return VR_ERR_STATE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  if (!is_device_pointer(grad_rgba)) return VR_ERR_INVALID_ARG;
+  if (grad_volume && !is_device_pointer(grad_volume)) return VR_ERR_INVALID_ARG;
+  if (grad_tf && !is_device_pointer(grad_tf)) return VR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nvox = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+  void* adj = ctx->adj;
+  st = ensure(ctx, &adj, &ctx->adj_cap, nvox * sizeof(float4));
+  if (st != VR_OK) return st;
+  ctx->adj = static_cast<float4*>(adj);
+  st = cuda_status(cudaMemsetAsync(ctx->adj, 0, nvox * sizeof(float4), s));
+  if (st != VR_OK) return st;
+  AdjointLaunch L;
+  L.V = vol_dev(ctx);
+  L.tf = tf_dev(ctx);
+  L.cam = ctx->camdev;
+  L.r = render_dev(ctx, params);
+  L.dtype = (int)ctx->dtype;
+  L.op = params->grad;
+  L.ck_kend = static_cast<const int*>(checkpoints);
+  L.ck_T = reinterpret_cast<const float*>(static_cast<const char*>(checkpoints) +
+                                          align256((size_t)rec->nrays * 4));
+  L.nslots = rec->nslots;
+  L.grad_rgba = reinterpret_cast<const float4*>(grad_rgba);
+  L.adj = grad_volume ? ctx->adj : nullptr;
+  L.grad_tf = grad_tf;
+  st = cuda_status(launch_adjoint(L, s));
+  if (st != VR_OK) return st;
+  if (grad_volume)
+    st = cuda_status(launch_adjoint_volume(ctx->adj, ctx->n, params->grad, 1.0f / ctx->value_max,
+                                           grad_volume, s));
+  return st;
+}
+
+vr_status vr_read_stats(vr_ctx* ctx, vr_stats* out, void* stream) {
+  if (!ctx || !out) return VR_ERR_INVALID_ARG;
+  if (!ctx->stats_valid) return VR_ERR_STATE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  unsigned long long h[4];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  vr_status st = cuda_status(cudaMemcpyAsync(h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+  if (st != VR_OK) return st;
+  st = cuda_status(cudaStreamSynchronize(s));
+  if (st != VR_OK) return st;
+  out->rays_hit = h[0];
+  out->samples_plain = h[1];
+  out->samples_visited = h[2];
+  out->samples_shaded = h[3];
+  return VR_OK;
+}
+
+const char* vr_status_string(vr_status s) {
+  switch (s) {
+    case VR_OK: return "ok";
+    case VR_ERR_INVALID_ARG: return "invalid argument";
+    case VR_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case VR_ERR_CUDA: return "CUDA error";
+    case VR_ERR_UNSUPPORTED: return "unsupported";
+    case VR_ERR_TIMEOUT: return "device-side wait timed out";
+    case VR_ERR_STATE: return "invalid call order or state";
+  }
+  return "unknown status";
+}
+
+const char* vr_last_cuda_error(void) { return g_cuda_err; }
+
+int vr_version(void) { return 100; }
+
+}  // extern "C"

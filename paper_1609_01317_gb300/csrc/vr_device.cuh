@@ -1,0 +1,786 @@
+// vr_device.cuh -- device-side building blocks of the ray march (sm_103a).
+//
+// Every function here is one step of the method in "Volume Raycasting mit OpenCL"
+// (Kopal 2011), §3.10: ray setup against the bounding box (§3.3, §3.6), trilinear
+// sampling (§3.4, Eq. 2), transfer-function lookup (§3.7), gradient operators (§3.5,
+// Eq. 3, Eq. 4), point-light Phong shading (§3.8, Listing 3) and front-to-back
+// compositing (§3.9, Eq. 6).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace vr {
+
+constexpr int kBrick = 8;       // brick edge in voxels (empty-space skipping, §5.3)
+constexpr int kBrickShift = 3;
+constexpr int kCkptStride = 32; // samples per adjoint checkpoint segment
+constexpr int kPadLo = 1;       // clamp-to-edge border below each axis
+constexpr int kPadHi = 2;       // ... and above (covers the 4^3 stencil of the last cell)
+
+enum Op { OP_CENTRAL = 0, OP_SOBEL = 1, OP_ZH = 2 };
+enum VType { VT_U8 = 0, VT_U16 = 1, VT_F16 = 2, VT_F32 = 3 };
+
+// Camera basis, computed on the host in FP32 with separately rounded operations.
+struct CamDev {
+  float eye[3], fwd[3], right[3], upv[3];
+  float ax, ay;
+  int ortho, width, height;
+};
+
+// Padded volume: element (x, y, z), x,y,z in [-1, n+1], at
+// (x + 1) + px * ((y + 1) + py * (z + 1)).
+struct VolDev {
+  const void* data;
+  int n[3];
+  int px, pxy;       // x pitch and slice pitch of the padded array, in elements
+  int py;            // padded rows per slice
+  float value_max;   // raw -> [0,1]
+  int nb[3];         // bricks per axis
+  const uint8_t* vis;  // per-brick visibility (1 = some sample may be non-transparent)
+};
+
+struct TfDev {
+  const float4* tf;
+  int n;
+  float scale;  // (n - 1) / value_max: raw value -> table coordinate
+};
+
+struct ShadeDev {
+  float ka, kd, ks, shininess;
+  float light[3];
+  int headlight;
+};
+
+struct RenderDev {
+  float step;
+  float ert;          // stop once 1 - T >= ert
+  int skip;           // empty-space skipping on/off
+  float lo[3], hi[3]; // sampling box: clip box intersected with [0, n-1]^3
+  float gscale;       // gradient operator scale / value_max
+  ShadeDev sh;
+};
+
+// ----------------------------------------------------------------------- voxel fetch
+template <int VTYPE> struct VoxelT;
+template <> struct VoxelT<VT_U8> { using T = uint8_t; };
+template <> struct VoxelT<VT_U16> { using T = uint16_t; };
+template <> struct VoxelT<VT_F16> { using T = __half; };
+template <> struct VoxelT<VT_F32> { using T = float; };
+
+template <int VTYPE>
+__device__ __forceinline__ float ldv(const typename VoxelT<VTYPE>::T* __restrict__ v, int off) {
+  if constexpr (VTYPE == VT_F16) {
+    return __half2float(__ldg(v + off));
+  } else {
+    return static_cast<float>(__ldg(v + off));
+  }
+}
+
+// --------------------------------------------------------------- ray setup (§3.3)
+// FP32 with every operation rounded on its own (no contraction), so that the integer
+// sample count K is the same on every IEEE-754 implementation of this convention.
+__device__ __forceinline__ float dot_rn(const float a[3], const float b[3]) {
+  float r = __fmul_rn(a[0], b[0]);
+  r = __fadd_rn(r, __fmul_rn(a[1], b[1]));
+  return __fadd_rn(r, __fmul_rn(a[2], b[2]));
+}
+
+// Returns true on a hit; K receives the sample count (midpoint rule), tn the entry.
+__device__ __forceinline__ bool ray_setup(const CamDev& c, const float lo[3], const float hi[3],
+                                          float step, int px, int py, float o[3], float d[3],
+                                          float& tn, int& K) {
+  const float sx = __fsub_rn(__fdiv_rn((float)(2 * px + 1), (float)c.width), 1.0f);
+  const float sy = __fsub_rn(1.0f, __fdiv_rn((float)(2 * py + 1), (float)c.height));
+  const float u = __fmul_rn(sx, c.ax), v = __fmul_rn(sy, c.ay);
+  if (c.ortho) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      o[a] = __fadd_rn(__fadd_rn(c.eye[a], __fmul_rn(u, c.right[a])), __fmul_rn(v, c.upv[a]));
+      d[a] = c.fwd[a];
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      d[a] = __fadd_rn(__fadd_rn(c.fwd[a], __fmul_rn(u, c.right[a])), __fmul_rn(v, c.upv[a]));
+      o[a] = c.eye[a];
+    }
+    const float l = __fsqrt_rn(dot_rn(d, d));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = __fdiv_rn(d[a], l);
+  }
+  float t0 = 0.0f, t1 = __int_as_float(0x7f800000);  // entry clamped to t >= 0
+  tn = 0.0f;
+  K = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (lo[a] > hi[a]) return false;
+    if (d[a] == 0.0f) {
+      if (o[a] < lo[a] || o[a] > hi[a]) return false;
+    } else {
+      const float ta = __fdiv_rn(__fsub_rn(lo[a], o[a]), d[a]);
+      const float tb = __fdiv_rn(__fsub_rn(hi[a], o[a]), d[a]);
+      const float tmin = ta < tb ? ta : tb, tmax = ta < tb ? tb : ta;
+      if (tmin > t0) t0 = tmin;
+      if (tmax < t1) t1 = tmax;
+    }
+  }
+  tn = t0;
+  if (!(t1 >= t0)) return false;
+  const float kf = floorf(__fadd_rn(__fdiv_rn(__fsub_rn(t1, t0), step), 0.5f));
+  K = kf > 0.0f ? (int)kf : 0;
+  return true;
+}
+
+// ------------------------------------------------------------------ cell (§3.4)
+struct Cell {
+  int base;          // padded offset of voxel (ix, iy, iz)
+  float f[3];        // fractional position inside the cell
+  int ib[3];         // integer cell coordinates
+};
+
+__device__ __forceinline__ Cell cell_of(const VolDev& V, const float p[3]) {
+  Cell c;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int i = (int)floorf(p[a]);
+    const int top = V.n[a] > 1 ? V.n[a] - 2 : 0;
+    i = i < 0 ? 0 : (i > top ? top : i);
+    c.ib[a] = i;
+    c.f[a] = p[a] - (float)i;
+  }
+  c.base = (c.ib[0] + kPadLo) + V.px * (c.ib[1] + kPadLo) + V.pxy * (c.ib[2] + kPadLo);
+  return c;
+}
+
+// lerp written as a + f (b - a): for integer voxels b - a is exact, so the result
+// stays inside [min(a,b), max(a,b)] (the empty-space test relies on this).
+__device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(f, b - a, a); }
+
+// Trilinear interpolation in raw units: lerps along x, then y, then z.
+template <int VTYPE>
+__device__ __forceinline__ float trilinear(const VolDev& V, const Cell& c) {
+  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
+  const int b = c.base, px = V.px, pxy = V.pxy;
+  const float c000 = ldv<VTYPE>(v, b), c100 = ldv<VTYPE>(v, b + 1);
+  const float c010 = ldv<VTYPE>(v, b + px), c110 = ldv<VTYPE>(v, b + px + 1);
+  const float c001 = ldv<VTYPE>(v, b + pxy), c101 = ldv<VTYPE>(v, b + pxy + 1);
+  const float c011 = ldv<VTYPE>(v, b + pxy + px), c111 = ldv<VTYPE>(v, b + pxy + px + 1);
+  const float x00 = lerpf(c000, c100, c.f[0]), x10 = lerpf(c010, c110, c.f[0]);
+  const float x01 = lerpf(c001, c101, c.f[0]), x11 = lerpf(c011, c111, c.f[0]);
+  const float y0 = lerpf(x00, x10, c.f[1]), y1 = lerpf(x01, x11, c.f[1]);
+  return lerpf(y0, y1, c.f[2]);
+}
+
+// ------------------------------------------------------------ transfer function
+struct TfSample {
+  float4 rgba;
+  int i;     // lower entry
+  float w;   // weight of entry i + 1
+  bool inside;  // u was not clamped (slope is defined)
+};
+
+// §3.7 lookup table read with linear interpolation between entries.
+__device__ __forceinline__ TfSample tf_lookup(const TfDev& tf, float s_raw) {
+  TfSample r;
+  float u = s_raw * tf.scale;
+  const float top = (float)(tf.n - 1);
+  r.inside = (u >= 0.0f) && (u <= top);
+  u = fminf(fmaxf(u, 0.0f), top);
+  int i = (int)u;
+  if (i > tf.n - 2) i = tf.n - 2;
+  r.i = i;
+  r.w = u - (float)i;
+  const float4 a = __ldg(tf.tf + i), b = __ldg(tf.tf + i + 1);
+  r.rgba.x = lerpf(a.x, b.x, r.w);
+  r.rgba.y = lerpf(a.y, b.y, r.w);
+  r.rgba.z = lerpf(a.z, b.z, r.w);
+  r.rgba.w = lerpf(a.w, b.w, r.w);
+  return r;
+}
+
+// ------------------------------------------------------------- gradient (§3.5)
+// The operators are linear and all taps of a sample share its fractional weights, so
+// the gradient at p equals the trilinear blend of the integer-grid operator evaluated at
+// the eight corners of p's cell.  With clamp-to-edge addressing that blend needs the
+// 4x4x4 voxel neighbourhood N[a][b][c] = E(i0 + (a-1, b-1, c-1)); it is contracted one
+// axis at a time with three 4-tap kernels per axis:
+//   T = [0, 1-f, f, 0]         (plain interpolation)
+//   U = [1-f, f, 1-f, f]       (the +-1 cross taps blended over the two corners)
+//   D = [-(1-f), -f, 1-f, f]   (the +-1 difference along the component's own axis)
+// An operator with plane weights W[b][c] = w0 d(b)d(c) + w1 (d(b)o(c) + o(b)d(c)) +
+// w2 o(b)o(c) (d = centre tap, o = the two outer taps) then gives, e.g. for x,
+//   g_x = D_x . (w0 T_yT_z + w1 (T_yU_z + U_yT_z) + w2 U_yU_z) . N.
+// Sobel3D (Eq. 4): w = (6, 3, 1).  Zucker-Hummel: w = (1, 1/sqrt2, 1/sqrt3).
+__device__ __forceinline__ float kT(float x0, float x1, float x2, float x3, float f) {
+  (void)x0; (void)x3;
+  return fmaf(f, x2 - x1, x1);
+}
+__device__ __forceinline__ float kU(float x0, float x1, float x2, float x3, float f) {
+  const float a = x0 + x2, b = x1 + x3;
+  return fmaf(f, b - a, a);
+}
+__device__ __forceinline__ float kD(float x0, float x1, float x2, float x3, float f) {
+  const float p = x2 - x0, q = x3 - x1;
+  return fmaf(f, q - p, p);
+}
+
+// Value (raw units) and unscaled operator gradient from the 4^3 neighbourhood.
+template <int VTYPE, int OP>
+__device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& c, float& s,
+                                                   float g[3]) {
+  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
+  const int px = V.px, pxy = V.pxy;
+  const int b0 = c.base - 1 - px - pxy;  // offset of N[0][0][0]
+  const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
+  if constexpr (OP == OP_CENTRAL) {
+    // Eq. 3 blended over the cell: only the cross-shaped 32-voxel subset is needed.
+    // zt[a][b] = T_z-contraction for b in {1,2}; all a.
+    float zt_x[4][2], zt_y[2][4], zd[2][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 1; b <= 2; ++b) {
+        const int o = b0 + a + b * px;
+        zt_x[a][b - 1] = kT(0.f, ldv<VTYPE>(v, o + pxy), ldv<VTYPE>(v, o + 2 * pxy), 0.f, fz);
+      }
+#pragma unroll
+    for (int a = 1; a <= 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (b == 1 || b == 2) {
+          zt_y[a - 1][b] = zt_x[a][b - 1];
+        } else {
+          const int o = b0 + a + b * px;
+          zt_y[a - 1][b] = kT(0.f, ldv<VTYPE>(v, o + pxy), ldv<VTYPE>(v, o + 2 * pxy), 0.f, fz);
+        }
+      }
+#pragma unroll
+    for (int a = 1; a <= 2; ++a)
+#pragma unroll
+      for (int b = 1; b <= 2; ++b) {
+        const int o = b0 + a + b * px;
+        const float n0 = ldv<VTYPE>(v, o), n3 = ldv<VTYPE>(v, o + 3 * pxy);
+        const float n1 = ldv<VTYPE>(v, o + pxy), n2 = ldv<VTYPE>(v, o + 2 * pxy);
+        zd[a - 1][b - 1] = kD(n0, n1, n2, n3, fz);
+      }
+    // x: D_x over a of (T_y over b of zt)
+    float yt[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) yt[a] = fmaf(fy, zt_x[a][1] - zt_x[a][0], zt_x[a][0]);
+    s = kT(yt[0], yt[1], yt[2], yt[3], fx);
+    g[0] = kD(yt[0], yt[1], yt[2], yt[3], fx);
+    float yd[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) yd[a] = kD(zt_y[a][0], zt_y[a][1], zt_y[a][2], zt_y[a][3], fy);
+    g[1] = fmaf(fx, yd[1] - yd[0], yd[0]);
+    const float z0 = fmaf(fy, zd[0][1] - zd[0][0], zd[0][0]);
+    const float z1 = fmaf(fy, zd[1][1] - zd[1][0], zd[1][0]);
+    g[2] = fmaf(fx, z1 - z0, z0);
+  } else {
+    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+    float Zt[4][4], Zu[4][4], Zd[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int o = b0 + a + b * px;
+        const float n0 = ldv<VTYPE>(v, o), n1 = ldv<VTYPE>(v, o + pxy);
+        const float n2 = ldv<VTYPE>(v, o + 2 * pxy), n3 = ldv<VTYPE>(v, o + 3 * pxy);
+        Zt[a][b] = kT(n0, n1, n2, n3, fz);
+        Zu[a][b] = kU(n0, n1, n2, n3, fz);
+        Zd[a][b] = kD(n0, n1, n2, n3, fz);
+      }
+    float ytt[4], yut[4], ydt[4], ytu[4], yuu[4], ydu[4], ytd[4], yud[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      ytt[a] = kT(Zt[a][0], Zt[a][1], Zt[a][2], Zt[a][3], fy);
+      yut[a] = kU(Zt[a][0], Zt[a][1], Zt[a][2], Zt[a][3], fy);
+      ydt[a] = kD(Zt[a][0], Zt[a][1], Zt[a][2], Zt[a][3], fy);
+      ytu[a] = kT(Zu[a][0], Zu[a][1], Zu[a][2], Zu[a][3], fy);
+      yuu[a] = kU(Zu[a][0], Zu[a][1], Zu[a][2], Zu[a][3], fy);
+      ydu[a] = kD(Zu[a][0], Zu[a][1], Zu[a][2], Zu[a][3], fy);
+      ytd[a] = kT(Zd[a][0], Zd[a][1], Zd[a][2], Zd[a][3], fy);
+      yud[a] = kU(Zd[a][0], Zd[a][1], Zd[a][2], Zd[a][3], fy);
+    }
+    s = kT(ytt[0], ytt[1], ytt[2], ytt[3], fx);
+    float ex[4], ey0[4], ey1[4], ez0[4], ez1[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      ex[a] = w0 * ytt[a] + w1 * (ytu[a] + yut[a]) + w2 * yuu[a];
+      ey0[a] = w0 * ydt[a] + w1 * ydu[a];
+      ey1[a] = w1 * ydt[a] + w2 * ydu[a];
+      ez0[a] = w0 * ytd[a] + w1 * yud[a];
+      ez1[a] = w1 * ytd[a] + w2 * yud[a];
+    }
+    g[0] = kD(ex[0], ex[1], ex[2], ex[3], fx);
+    g[1] = kT(ey0[0], ey0[1], ey0[2], ey0[3], fx) + kU(ey1[0], ey1[1], ey1[2], ey1[3], fx);
+    g[2] = kT(ez0[0], ez0[1], ez0[2], ez0[3], fx) + kU(ez1[0], ez1[1], ez1[2], ez1[3], fx);
+  }
+}
+
+// ----------------------------------------------- per-ray neighbourhood cache (§3.5)
+// Along a ray every cell coordinate moves monotonically in the direction of travel, so
+// consecutive samples share most of their 4x4x4 neighbourhood.  The neighbourhood is
+// kept in registers in "travel order" (index 0 is the voxel behind the cell along the
+// ray's direction on that axis, 3 the one ahead); when the cell advances by one on an
+// axis, the cache shifts by one and only the new face is loaded.  In travel order the
+// interpolation kernels keep their form with f' = f (forward axis) or 1 - f (backward
+// axis); the difference kernel D changes sign on a backward axis.
+//
+// Central differences need only the cross-shaped subset of the neighbourhood: the
+// entries with at most one index on the outer layer {0, 3}.
+template <int OP>
+__host__ __device__ constexpr bool hood_needed(int a, int b, int c) {
+  return OP != OP_CENTRAL ||
+         ((a == 0 || a == 3) + (b == 0 || b == 3) + (c == 0 || c == 3)) <= 1;
+}
+
+struct Hood {
+  float N[4][4][4];
+  int ci[3];     // cached cell (travel order irrelevant), ci[0] = INT_MIN: empty
+  int off[3][4]; // element offsets of travel-order index i on each axis
+};
+
+__device__ __forceinline__ void hood_init(Hood& h, const VolDev& V, const float d[3]) {
+  const int pitch[3] = {1, V.px, V.pxy};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h.off[a][i] = (d[a] >= 0.0f ? i - 1 : 2 - i) * pitch[a];
+  h.ci[0] = h.ci[1] = h.ci[2] = -0x40000000;
+}
+
+__device__ __forceinline__ bool hood_in_set_rt(int op, int a, int b, int c) {
+  return op != OP_CENTRAL ||
+         ((a == 0 || a == 3) + (b == 0 || b == 3) + (c == 0 || c == 3)) <= 1;
+}
+
+// Bring the cache to cell c (base = padded offset of the cell's voxel).  A move of one
+// cell per axis (in the direction of travel) shifts the cache: after the shifts entry
+// (i,j,k) holds the old entry (i+mx, j+my, k+mz); every needed entry whose source lies
+// outside the cache or outside the needed set is then reloaded.  Larger moves (after a
+// skip) reload everything.
+template <int VTYPE, int OP>
+__device__ __forceinline__ void hood_update(Hood& h, const VolDev& V, const Cell& c,
+                                            const float d[3]) {
+  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
+  int mv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) mv[a] = d[a] >= 0.0f ? c.ib[a] - h.ci[a] : h.ci[a] - c.ib[a];
+  if ((mv[0] | mv[1] | mv[2]) == 0) return;
+  const bool shift = (unsigned)mv[0] <= 1u && (unsigned)mv[1] <= 1u && (unsigned)mv[2] <= 1u;
+  const int b = c.base;
+  if (!shift) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (hood_needed<OP>(i, j, k))
+            h.N[i][j][k] = ldv<VTYPE>(v, b + h.off[0][i] + h.off[1][j] + h.off[2][k]);
+  } else {
+    if (mv[0]) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) h.N[i][j][k] = h.N[i + 1][j][k];
+    }
+    if (mv[1]) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) h.N[i][j][k] = h.N[i][j + 1][k];
+    }
+    if (mv[2]) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) h.N[i][j][k] = h.N[i][j][k + 1];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!hood_needed<OP>(i, j, k)) continue;
+          const int si = i + mv[0], sj = j + mv[1], sk = k + mv[2];
+          const bool src_ok = si <= 3 && sj <= 3 && sk <= 3 && hood_in_set_rt(OP, si, sj, sk);
+          if (!src_ok) h.N[i][j][k] = ldv<VTYPE>(v, b + h.off[0][i] + h.off[1][j] + h.off[2][k]);
+        }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) h.ci[a] = c.ib[a];
+}
+
+// Travel-order fractions.
+__device__ __forceinline__ void hood_frac(const Cell& c, const float d[3], float fp[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) fp[a] = d[a] >= 0.0f ? c.f[a] : 1.0f - c.f[a];
+}
+
+// Trilinear value from the cache (inner 2x2x2, x then y then z).
+__device__ __forceinline__ float hood_value(const Hood& h, const float fp[3]) {
+  const float x00 = lerpf(h.N[1][1][1], h.N[2][1][1], fp[0]);
+  const float x10 = lerpf(h.N[1][2][1], h.N[2][2][1], fp[0]);
+  const float x01 = lerpf(h.N[1][1][2], h.N[2][1][2], fp[0]);
+  const float x11 = lerpf(h.N[1][2][2], h.N[2][2][2], fp[0]);
+  const float y0 = lerpf(x00, x10, fp[1]), y1 = lerpf(x01, x11, fp[1]);
+  return lerpf(y0, y1, fp[2]);
+}
+
+// Unscaled operator gradient from the cache (world axes; see value_and_gradient for the
+// contraction scheme).
+template <int OP>
+__device__ __forceinline__ void hood_gradient(const Hood& h, const float fp[3], const float d[3],
+                                              float g[3]) {
+  const float fx = fp[0], fy = fp[1], fz = fp[2];
+  if constexpr (OP == OP_CENTRAL) {
+    float yt[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float z1 = kT(0.f, h.N[a][1][1], h.N[a][1][2], 0.f, fz);
+      const float z2 = kT(0.f, h.N[a][2][1], h.N[a][2][2], 0.f, fz);
+      yt[a] = fmaf(fy, z2 - z1, z1);
+    }
+    g[0] = kD(yt[0], yt[1], yt[2], yt[3], fx);
+    float yd[2];
+#pragma unroll
+    for (int a = 1; a <= 2; ++a) {
+      float zt[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) zt[b] = kT(0.f, h.N[a][b][1], h.N[a][b][2], 0.f, fz);
+      yd[a - 1] = kD(zt[0], zt[1], zt[2], zt[3], fy);
+    }
+    g[1] = fmaf(fx, yd[1] - yd[0], yd[0]);
+    float zd[2][2];
+#pragma unroll
+    for (int a = 1; a <= 2; ++a)
+#pragma unroll
+      for (int b = 1; b <= 2; ++b)
+        zd[a - 1][b - 1] = kD(h.N[a][b][0], h.N[a][b][1], h.N[a][b][2], h.N[a][b][3], fz);
+    const float z0 = fmaf(fy, zd[0][1] - zd[0][0], zd[0][0]);
+    const float z1 = fmaf(fy, zd[1][1] - zd[1][0], zd[1][0]);
+    g[2] = fmaf(fx, z1 - z0, z0);
+  } else {
+    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+    float ex[4], ey0[4], ey1[4], ez0[4], ez1[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float zt[4], zu[4], zd[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float n0 = h.N[a][b][0], n1 = h.N[a][b][1], n2 = h.N[a][b][2], n3 = h.N[a][b][3];
+        zt[b] = kT(n0, n1, n2, n3, fz);
+        zu[b] = kU(n0, n1, n2, n3, fz);
+        zd[b] = kD(n0, n1, n2, n3, fz);
+      }
+      const float ytt = kT(zt[0], zt[1], zt[2], zt[3], fy);
+      const float yut = kU(zt[0], zt[1], zt[2], zt[3], fy);
+      const float ydt = kD(zt[0], zt[1], zt[2], zt[3], fy);
+      const float ytu = kT(zu[0], zu[1], zu[2], zu[3], fy);
+      const float yuu = kU(zu[0], zu[1], zu[2], zu[3], fy);
+      const float ydu = kD(zu[0], zu[1], zu[2], zu[3], fy);
+      const float ytd = kT(zd[0], zd[1], zd[2], zd[3], fy);
+      const float yud = kU(zd[0], zd[1], zd[2], zd[3], fy);
+      ex[a] = w0 * ytt + w1 * (ytu + yut) + w2 * yuu;
+      ey0[a] = w0 * ydt + w1 * ydu;
+      ey1[a] = w1 * ydt + w2 * ydu;
+      ez0[a] = w0 * ytd + w1 * yud;
+      ez1[a] = w1 * ytd + w2 * yud;
+    }
+    g[0] = kD(ex[0], ex[1], ex[2], ex[3], fx);
+    g[1] = kT(ey0[0], ey0[1], ey0[2], ey0[3], fx) + kU(ey1[0], ey1[1], ey1[2], ey1[3], fx);
+    g[2] = kT(ez0[0], ez0[1], ez0[2], ez0[3], fx) + kU(ez1[0], ez1[1], ez1[2], ez1[3], fx);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[a] = d[a] >= 0.0f ? g[a] : -g[a];
+}
+
+// ------------------------------------------- per-ray neighbourhood ring buffer (§3.5)
+// Consecutive samples of a ray share most of their 4x4x4 neighbourhood.  Each thread
+// keeps its ray's neighbourhood in shared memory as a ring indexed by voxel coordinate
+// mod 4: voxel (X, Y, Z) lives in column (X & 3, Y & 3), lane (Z & 3) of a float4.  When
+// the cell advances by one voxel on an axis, the voxels leaving the neighbourhood occupy
+// exactly the slots of the ones entering it, so an advance only loads the new face; a
+// larger jump (after a skip) reloads the whole neighbourhood.  Columns are read as float4
+// in slot order; the z kernels are rotated to slot order instead of the data.
+//
+// Layout: ring[(xs * 4 + ys) * kRingStride + tid], one float4 per column and thread, so a
+// warp's accesses to the same column are consecutive float4s (no bank conflicts).
+struct Ring {
+  float4* base;  // &ring[tid]
+  int stride;    // threads per block (float4 units between columns)
+  int ci[3];     // cached cell, ci[0] = INT_MIN when empty
+};
+
+__device__ __forceinline__ float4& ring_col(const Ring& r, int xs, int ys) {
+  return r.base[(xs * 4 + ys) * r.stride];
+}
+
+// Load the 4 z-voxels of column (X = cell + a - 1, Y = cell + b - 1) in slot order:
+// slot q holds Z = cz - 1 + ((q - rz) & 3) with rz = (cz - 1) & 3.
+template <int VTYPE>
+__device__ __forceinline__ float4 load_column(const typename VoxelT<VTYPE>::T* __restrict__ v,
+                                              int colbase, int rz, int pxy) {
+  float e[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[q] = ldv<VTYPE>(v, colbase + (((q - rz) & 3) - 1) * pxy);
+  return make_float4(e[0], e[1], e[2], e[3]);
+}
+
+template <int VTYPE>
+__device__ __forceinline__ void ring_update(Ring& r, const VolDev& V, const Cell& c) {
+  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
+  const int dx = c.ib[0] - r.ci[0], dy = c.ib[1] - r.ci[1], dz = c.ib[2] - r.ci[2];
+  if ((dx | dy | dz) == 0) return;
+  const int px = V.px, pxy = V.pxy;
+  const int rx = (c.ib[0] - 1) & 3, ry = (c.ib[1] - 1) & 3, rz = (c.ib[2] - 1) & 3;
+  const int b0 = c.base - 1 - px;  // offset of (X = cx-1, Y = cy-1, Z = cz)
+  const bool small = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
+  if (!small) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        ring_col(r, (rx + a) & 3, (ry + b) & 3) = load_column<VTYPE>(v, b0 + a + b * px, rz, pxy);
+  } else {
+    if (dx != 0) {
+      const int a = dx > 0 ? 3 : 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        ring_col(r, (rx + a) & 3, (ry + b) & 3) = load_column<VTYPE>(v, b0 + a + b * px, rz, pxy);
+    }
+    if (dy != 0) {
+      const int b = dy > 0 ? 3 : 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        ring_col(r, (rx + a) & 3, (ry + b) & 3) = load_column<VTYPE>(v, b0 + a + b * px, rz, pxy);
+    }
+    if (dz != 0) {
+      const int cz = dz > 0 ? 3 : 0;
+      const int q = (rz + cz) & 3;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          float* col = reinterpret_cast<float*>(&ring_col(r, (rx + a) & 3, (ry + b) & 3));
+          col[q] = ldv<VTYPE>(v, b0 + a + b * px + (cz - 1) * pxy);
+        }
+    }
+  }
+  r.ci[0] = c.ib[0];
+  r.ci[1] = c.ib[1];
+  r.ci[2] = c.ib[2];
+}
+
+// 4-tap weights of T, U and D along z, rotated to slot order (slot q <- tap (q - rz) & 3).
+struct ZWeights {
+  float t[4], u[4], d[4];
+};
+
+__device__ __forceinline__ float rot4(float w0, float w1, float w2, float w3, int q, int rz) {
+  const int c = (q - rz) & 3;
+  const float lo = (c & 1) ? w1 : w0, hi = (c & 1) ? w3 : w2;
+  return (c & 2) ? hi : lo;
+}
+
+__device__ __forceinline__ ZWeights z_weights(float fz, int rz) {
+  ZWeights w;
+  const float g = 1.0f - fz;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    w.t[q] = rot4(0.0f, g, fz, 0.0f, q, rz);
+    w.u[q] = rot4(g, fz, g, fz, q, rz);
+    w.d[q] = rot4(-g, -fz, g, fz, q, rz);
+  }
+  return w;
+}
+
+__device__ __forceinline__ float dot4(const float w[4], const float4& x) {
+  return fmaf(w[3], x.w, fmaf(w[2], x.z, fmaf(w[1], x.y, w[0] * x.x)));
+}
+
+// Trilinear value (raw units) from the ring.
+__device__ __forceinline__ float ring_value(const Ring& r, const Cell& c, const ZWeights& zw) {
+  const int rx = (c.ib[0] - 1) & 3, ry = (c.ib[1] - 1) & 3;
+  float zt[2][2];
+#pragma unroll
+  for (int a = 1; a <= 2; ++a)
+#pragma unroll
+    for (int b = 1; b <= 2; ++b) zt[a - 1][b - 1] = dot4(zw.t, ring_col(r, (rx + a) & 3, (ry + b) & 3));
+  const float y0 = lerpf(zt[0][0], zt[0][1], c.f[1]);
+  const float y1 = lerpf(zt[1][0], zt[1][1], c.f[1]);
+  return lerpf(y0, y1, c.f[0]);
+}
+
+// Unscaled operator gradient from the ring (see value_and_gradient for the scheme).
+template <int OP>
+__device__ __forceinline__ void ring_gradient(const Ring& r, const Cell& c, const ZWeights& zw,
+                                              float g[3]) {
+  const int rx = (c.ib[0] - 1) & 3, ry = (c.ib[1] - 1) & 3;
+  const float fx = c.f[0], fy = c.f[1];
+  if constexpr (OP == OP_CENTRAL) {
+    float yt[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float z1 = dot4(zw.t, ring_col(r, (rx + a) & 3, (ry + 1) & 3));
+      const float z2 = dot4(zw.t, ring_col(r, (rx + a) & 3, (ry + 2) & 3));
+      yt[a] = lerpf(z1, z2, fy);
+    }
+    g[0] = kD(yt[0], yt[1], yt[2], yt[3], fx);
+    float yd[2];
+#pragma unroll
+    for (int a = 1; a <= 2; ++a) {
+      float zt[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) zt[b] = dot4(zw.t, ring_col(r, (rx + a) & 3, (ry + b) & 3));
+      yd[a - 1] = kD(zt[0], zt[1], zt[2], zt[3], fy);
+    }
+    g[1] = lerpf(yd[0], yd[1], fx);
+    float zd[2][2];
+#pragma unroll
+    for (int a = 1; a <= 2; ++a)
+#pragma unroll
+      for (int b = 1; b <= 2; ++b)
+        zd[a - 1][b - 1] = dot4(zw.d, ring_col(r, (rx + a) & 3, (ry + b) & 3));
+    const float z0 = lerpf(zd[0][0], zd[0][1], fy);
+    const float z1 = lerpf(zd[1][0], zd[1][1], fy);
+    g[2] = lerpf(z0, z1, fx);
+  } else {
+    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+    float ex[4], ey0[4], ey1[4], ez0[4], ez1[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float zt[4], zu[4], zd[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float4 col = ring_col(r, (rx + a) & 3, (ry + b) & 3);
+        zt[b] = dot4(zw.t, col);
+        zu[b] = dot4(zw.u, col);
+        zd[b] = dot4(zw.d, col);
+      }
+      const float ytt = kT(zt[0], zt[1], zt[2], zt[3], fy);
+      const float yut = kU(zt[0], zt[1], zt[2], zt[3], fy);
+      const float ydt = kD(zt[0], zt[1], zt[2], zt[3], fy);
+      const float ytu = kT(zu[0], zu[1], zu[2], zu[3], fy);
+      const float yuu = kU(zu[0], zu[1], zu[2], zu[3], fy);
+      const float ydu = kD(zu[0], zu[1], zu[2], zu[3], fy);
+      const float ytd = kT(zd[0], zd[1], zd[2], zd[3], fy);
+      const float yud = kU(zd[0], zd[1], zd[2], zd[3], fy);
+      ex[a] = fmaf(w0, ytt, fmaf(w1, ytu + yut, w2 * yuu));
+      ey0[a] = fmaf(w0, ydt, w1 * ydu);
+      ey1[a] = fmaf(w1, ydt, w2 * ydu);
+      ez0[a] = fmaf(w0, ytd, w1 * yud);
+      ez1[a] = fmaf(w1, ytd, w2 * yud);
+    }
+    g[0] = kD(ex[0], ex[1], ex[2], ex[3], fx);
+    g[1] = kT(ey0[0], ey0[1], ey0[2], ey0[3], fx) + kU(ey1[0], ey1[1], ey1[2], ey1[3], fx);
+    g[2] = kT(ez0[0], ez0[1], ez0[2], ez0[3], fx) + kU(ez1[0], ez1[1], ez1[2], ez1[3], fx);
+  }
+}
+
+// Scale of each operator: 1 / (2 * sum of one side's weights).
+__host__ __device__ constexpr float op_scale(int op) {
+  return op == OP_CENTRAL ? 0.5f
+       : op == OP_SOBEL   ? (1.0f / 44.0f)
+                          : (float)(1.0 / (2.0 * (1.0 + 4.0 / 1.4142135623730951 +
+                                                  4.0 / 1.7320508075688772)));
+}
+
+// --------------------------------------------------------------------- shading
+struct ShadeOut {
+  float c[3];
+  float N[3], L[3], V[3];
+  float nl, rv, gl;  // N.L, R.V, |g_hat|
+};
+
+// Outward normal N = -g/|g| (zero below 1e-6), point light and Phong (§3.8).
+__device__ __forceinline__ void shade(const ShadeDev& sh, const CamDev& cam, const float d[3],
+                                      const float p[3], const float gh[3], const float4& rgba,
+                                      ShadeOut& r) {
+  const float g2 = gh[0] * gh[0] + gh[1] * gh[1] + gh[2] * gh[2];
+  r.gl = sqrtf(g2);
+  if (g2 > 1e-12f) {
+    const float inv = -rsqrtf(g2);
+    r.N[0] = gh[0] * inv; r.N[1] = gh[1] * inv; r.N[2] = gh[2] * inv;
+  } else {
+    r.N[0] = r.N[1] = r.N[2] = 0.0f;
+  }
+  float lp[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) lp[a] = (sh.headlight ? cam.eye[a] : sh.light[a]) - p[a];
+  const float il = rsqrtf(lp[0] * lp[0] + lp[1] * lp[1] + lp[2] * lp[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r.L[a] = lp[a] * il;
+  if (cam.ortho) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r.V[a] = -d[a];
+  } else if (sh.headlight) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r.V[a] = r.L[a];
+  } else {
+    float e[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) e[a] = cam.eye[a] - p[a];
+    const float ie = rsqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r.V[a] = e[a] * ie;
+  }
+  const float nl = r.N[0] * r.L[0] + r.N[1] * r.L[1] + r.N[2] * r.L[2];
+  r.nl = nl;
+  const float diff = fmaxf(nl, 0.0f);
+  float spec = 0.0f;
+  r.rv = 0.0f;
+  if (nl > 0.0f) {
+    const float nv = r.N[0] * r.V[0] + r.N[1] * r.V[1] + r.N[2] * r.V[2];
+    const float lv = r.L[0] * r.V[0] + r.L[1] * r.V[1] + r.L[2] * r.V[2];
+    const float rv = 2.0f * nl * nv - lv;  // R.V with R = 2 (N.L) N - L
+    r.rv = rv;
+    if (rv > 0.0f) spec = __powf(rv, sh.shininess);
+  }
+  const float k = fmaf(sh.kd, diff, sh.ka);
+  r.c[0] = fmaf(rgba.x, k, sh.ks * spec);
+  r.c[1] = fmaf(rgba.y, k, sh.ks * spec);
+  r.c[2] = fmaf(rgba.z, k, sh.ks * spec);
+}
+
+// Index of the brick containing p (clamped to the brick grid).
+__device__ __forceinline__ int brick_of(const VolDev& V, const float p[3], int b[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int i = ((int)floorf(p[a])) >> kBrickShift;
+    b[a] = i < 0 ? 0 : (i >= V.nb[a] ? V.nb[a] - 1 : i);
+  }
+  return b[0] + V.nb[0] * (b[1] + V.nb[1] * b[2]);
+}
+
+// First sample index whose t lies at or beyond the exit of brick b (§5.3 skipping; the
+// brick footprint tables cover one voxel around the brick, so rounding of t is harmless).
+__device__ __forceinline__ int brick_exit_sample(const int b[3], const float o[3],
+                                                 const float d[3], float tn, float step) {
+  float te = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] > 0.0f) te = fminf(te, ((float)((b[a] + 1) << kBrickShift) - o[a]) / d[a]);
+    else if (d[a] < 0.0f) te = fminf(te, ((float)(b[a] << kBrickShift) - o[a]) / d[a]);
+  }
+  const float kf = ceilf((te - tn) / step - 0.5f);
+  return kf > 2.0e9f ? 2000000000 : (int)kf;
+}
+
+}  // namespace vr

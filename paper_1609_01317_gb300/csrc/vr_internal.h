@@ -1,0 +1,131 @@
+// vr_internal.h -- host-side context and launcher declarations of libvr.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/vr.h"
+#include "vr_device.cuh"
+
+namespace vr {
+
+// One forward pass that wrote adjoint checkpoints (remembered to validate the backward).
+struct CkptRecord {
+  const void* ptr = nullptr;
+  size_t bytes = 0;
+  vr_camera cam{};
+  vr_render_params params{};
+  uint64_t vol_gen = 0, tf_gen = 0;
+  int nrays = 0, nslots = 0;
+};
+
+constexpr int kMaxCkptRecords = 128;
+
+}  // namespace vr
+
+struct vr_ctx {
+  int device = 0;
+  vr_alloc_fn alloc = nullptr;
+  vr_free_fn free_fn = nullptr;
+  void* user = nullptr;
+
+  // volume (padded copy with clamp-to-edge border) and brick tables
+  bool has_volume = false;
+  vr_dtype dtype = VR_U8;
+  int n[3] = {0, 0, 0};
+  float value_max = 1.0f;
+  void* vol = nullptr;
+  size_t vol_cap = 0;
+  int px = 0, py = 0, pz = 0;  // padded extents
+  int nb[3] = {0, 0, 0};
+  float2* brick_minmax = nullptr;
+  uint8_t* brick_vis = nullptr;
+  size_t brick_cap = 0;
+  void* upload_staging = nullptr;
+  size_t upload_cap = 0;
+
+  // transfer function
+  bool has_tf = false;
+  int ntf = 0;
+  float4* tf = nullptr;
+  size_t tf_cap = 0;
+  int* tf_prefix = nullptr;  // number of entries with alpha != 0 below each index
+  uint64_t vol_gen = 0, tf_gen = 0;
+
+  // camera
+  bool has_camera = false;
+  vr_camera cam{};
+  vr::CamDev camdev{};
+
+  // statistics
+  unsigned long long* stats = nullptr;
+  bool stats_valid = false;
+
+  // output staging for host destinations
+  void* out_staging = nullptr;
+  size_t out_cap = 0;
+
+  // adjoint scratch: per voxel (dL/ds, dL/dG) at the cell corners, float4
+  float4* adj = nullptr;
+  size_t adj_cap = 0;
+
+  vr::CkptRecord ckpt[vr::kMaxCkptRecords];
+  int ckpt_next = 0;
+};
+
+namespace vr {
+
+// allocation through the context's allocator
+vr_status ctx_alloc(vr_ctx* ctx, void** p, size_t bytes);
+void ctx_free(vr_ctx* ctx, void* p);
+vr_status ensure(vr_ctx* ctx, void** p, size_t* cap, size_t bytes);
+vr_status cuda_status(cudaError_t e);
+
+// device descriptors
+VolDev vol_dev(const vr_ctx* ctx);
+TfDev tf_dev(const vr_ctx* ctx);
+RenderDev render_dev(const vr_ctx* ctx, const vr_render_params* p);
+int max_samples(const vr_ctx* ctx, const vr_render_params* p);
+
+// launchers (return the first CUDA error, if any)
+cudaError_t launch_pad_volume(const void* src, int dtype, const int n[3], void* dst, int px,
+                              int py, int pz, cudaStream_t s);
+cudaError_t launch_brick_minmax(const VolDev& V, int dtype, float2* mm, cudaStream_t s);
+cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t s);
+cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
+                                    int ntf, float scale, uint8_t* vis, cudaStream_t s);
+
+struct MarchLaunch {
+  VolDev V;
+  TfDev tf;
+  CamDev cam;
+  RenderDev r;
+  int dtype, op;
+  float4* out;
+  unsigned long long* stats;  // NULL: no counting
+  int* ck_kend;               // NULL: no checkpoints
+  float* ck_T;
+  int nslots;
+};
+cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s);
+
+struct AdjointLaunch {
+  VolDev V;
+  TfDev tf;
+  CamDev cam;
+  RenderDev r;
+  int dtype, op;
+  const int* ck_kend;
+  const float* ck_T;
+  int nslots;
+  const float4* grad_rgba;
+  float4* adj;     // per voxel corner accumulators (dL/ds, dL/dG) over the unpadded grid
+  float* grad_tf;  // n x 4, accumulated
+};
+cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t s);
+cudaError_t launch_adjoint_volume(const float4* adj, const int n[3], int op, float inv_vmax,
+                                  float* grad_volume, cudaStream_t s);
+
+}  // namespace vr

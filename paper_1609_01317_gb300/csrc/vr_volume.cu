@@ -1,0 +1,213 @@
+// vr_volume.cu -- volume upload kernels: clamp-to-edge padded copy, per-brick min/max
+// footprints and per-brick visibility for empty-space skipping (§5.3, §5.4).
+#include "vr_internal.h"
+
+namespace vr {
+
+// ---------------------------------------------------------------- padded copy
+// dst element (x, y, z), x in [0, px), holds src(clamp(x-1), clamp(y-1), clamp(z-1)):
+// the clamp-to-edge extension the gradient taps read beyond the volume (§3.6: gradients
+// use voxels before the ray start).  One warp per destination row; each lane writes 8
+// consecutive elements with one vector store (px is a multiple of 16 elements).
+template <typename T, typename V>
+__global__ void k_pad(const T* __restrict__ src, int nx, int ny, int nz, T* __restrict__ dst,
+                      int px, int py, int pz) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int rows = py * pz;
+  if (warp >= rows) return;
+  const int y = warp % py, z = warp / py;
+  int sy = y - kPadLo, sz = z - kPadLo;
+  sy = sy < 0 ? 0 : (sy >= ny ? ny - 1 : sy);
+  sz = sz < 0 ? 0 : (sz >= nz ? nz - 1 : sz);
+  const T* srow = src + ((size_t)sz * ny + sy) * nx;
+  T* drow = dst + (size_t)warp * px;
+  constexpr int kPer = 8;
+  static_assert(sizeof(V) * (kPer * sizeof(T) / sizeof(V)) == kPer * sizeof(T), "vector");
+  for (int x0 = lane * kPer; x0 < px; x0 += 32 * kPer) {
+    union {
+      T e[kPer];
+      V v[kPer * sizeof(T) / sizeof(V)];
+    } u;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      int sx = x0 + j - kPadLo;
+      sx = sx < 0 ? 0 : (sx >= nx ? nx - 1 : sx);
+      u.e[j] = srow[sx];
+    }
+#pragma unroll
+    for (int j = 0; j < (int)(kPer * sizeof(T) / sizeof(V)); ++j)
+      reinterpret_cast<V*>(drow + x0)[j] = u.v[j];
+  }
+}
+
+cudaError_t launch_pad_volume(const void* src, int dtype, const int n[3], void* dst, int px,
+                              int py, int pz, cudaStream_t s) {
+  const long rows = (long)py * pz;
+  const int threads = 256;
+  const int blocks = (int)((rows * 32 + threads - 1) / threads);
+  switch (dtype) {
+    case VT_U8:
+      k_pad<uint8_t, uint2><<<blocks, threads, 0, s>>>((const uint8_t*)src, n[0], n[1], n[2],
+                                                       (uint8_t*)dst, px, py, pz);
+      break;
+    case VT_U16:
+    case VT_F16:
+      k_pad<uint16_t, uint4><<<blocks, threads, 0, s>>>((const uint16_t*)src, n[0], n[1], n[2],
+                                                        (uint16_t*)dst, px, py, pz);
+      break;
+    default:
+      k_pad<float, uint4><<<blocks, threads, 0, s>>>((const float*)src, n[0], n[1], n[2],
+                                                     (float*)dst, px, py, pz);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- brick min / max
+// Brick (bx, by, bz) covers voxels [8b, 8b+8) per axis.  Its footprint is
+// [8b - 1, 8b + 9] (clipped to the volume): every sample whose position lies within one
+// voxel of the brick box interpolates only voxels from it.  One warp per brick; each
+// lane reduces whole footprint rows, read as aligned vectors: in padded coordinates a
+// row of the footprint starts at x = 8 bx, a multiple of 8 elements, and the row pitch
+// is a multiple of 16 elements, so the loads below stay inside the padded row.
+template <int VTYPE>
+__device__ __forceinline__ void row_minmax(const void* base, int lo, int hi, float& vmin,
+                                           float& vmax) {
+  float e[12];
+  if constexpr (VTYPE == VT_U8) {
+    const uint2 a = *reinterpret_cast<const uint2*>(base);
+    const uint2 b = hi >= 8 ? *(reinterpret_cast<const uint2*>(base) + 1) : make_uint2(0, 0);
+    const unsigned w[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+    for (int j = 0; j < 12; ++j) e[j] = (float)((w[j >> 2] >> (8 * (j & 3))) & 0xffu);
+  } else if constexpr (VTYPE == VT_U16 || VTYPE == VT_F16) {
+    const uint4 a = *reinterpret_cast<const uint4*>(base);
+    const uint4 b = hi >= 8 ? *(reinterpret_cast<const uint4*>(base) + 1) : make_uint4(0, 0, 0, 0);
+    const unsigned w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const unsigned short h = (unsigned short)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+      if constexpr (VTYPE == VT_U16) e[j] = (float)h;
+      else e[j] = __half2float(__ushort_as_half(h));
+    }
+  } else {
+    const float4 a = *reinterpret_cast<const float4*>(base);
+    const float4 b = *(reinterpret_cast<const float4*>(base) + 1);
+    const float4 c = hi >= 8 ? *(reinterpret_cast<const float4*>(base) + 2) : make_float4(0, 0, 0, 0);
+    const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int j = 0; j < 12; ++j) e[j] = w[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 11; ++j) {
+    if (j >= lo && j <= hi) {
+      vmin = fminf(vmin, e[j]);
+      vmax = fmaxf(vmax, e[j]);
+    }
+  }
+}
+
+template <int VTYPE>
+__global__ void k_brick_minmax(const VolDev V, float2* __restrict__ mm, int nbricks) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nbricks) return;
+  const int bx = warp % V.nb[0];
+  const int by = (warp / V.nb[0]) % V.nb[1];
+  const int bz = warp / (V.nb[0] * V.nb[1]);
+  // footprint in padded coordinates (padded = voxel + 1)
+  const int x0 = bx << kBrickShift;  // padded x of voxel 8bx - 1
+  const int xlo = max((bx << kBrickShift) - 1, 0) + kPadLo - x0;
+  const int xhi = min((bx << kBrickShift) + kBrick + 1, V.n[0] - 1) + kPadLo - x0;
+  const int ylo = max((by << kBrickShift) - 1, 0), yhi = min((by << kBrickShift) + kBrick + 1, V.n[1] - 1);
+  const int zlo = max((bz << kBrickShift) - 1, 0), zhi = min((bz << kBrickShift) + kBrick + 1, V.n[2] - 1);
+  const int ey = yhi - ylo + 1, nrows = ey * (zhi - zlo + 1);
+  constexpr int esize = (VTYPE == VT_U8) ? 1 : ((VTYPE == VT_F32) ? 4 : 2);
+  const char* data = static_cast<const char*>(V.data);
+  float vmin = __int_as_float(0x7f800000), vmax = -vmin;
+  for (int r = lane; r < nrows; r += 32) {
+    const int y = ylo + r % ey, z = zlo + r / ey;
+    const size_t off = (size_t)x0 + (size_t)V.px * (y + kPadLo) + (size_t)V.pxy * (z + kPadLo);
+    row_minmax<VTYPE>(data + off * esize, xlo, xhi, vmin, vmax);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  }
+  if (lane == 0) mm[warp] = make_float2(vmin, vmax);
+}
+
+cudaError_t launch_brick_minmax(const VolDev& V, int dtype, float2* mm, cudaStream_t s) {
+  const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
+  const int threads = 256;
+  const int blocks = (nbricks * 32 + threads - 1) / threads;
+  switch (dtype) {
+    case VT_U8: k_brick_minmax<VT_U8><<<blocks, threads, 0, s>>>(V, mm, nbricks); break;
+    case VT_U16: k_brick_minmax<VT_U16><<<blocks, threads, 0, s>>>(V, mm, nbricks); break;
+    case VT_F16: k_brick_minmax<VT_F16><<<blocks, threads, 0, s>>>(V, mm, nbricks); break;
+    default: k_brick_minmax<VT_F32><<<blocks, threads, 0, s>>>(V, mm, nbricks);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ TF prefix counts
+// prefix[i] = number of entries j < i with alpha != 0 (prefix has n + 1 entries).
+// One block: each thread counts a contiguous chunk, then a shared-memory scan.
+__global__ void k_tf_prefix(const float4* __restrict__ tf, int n, int* __restrict__ prefix) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int chunk = (n + nt - 1) / nt;
+  const int i0 = t * chunk, i1 = min(i0 + chunk, n);
+  int c = 0;
+  for (int i = i0; i < i1; ++i) c += (tf[i].w != 0.0f);
+  part[t] = c;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    const int add = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += add;
+    __syncthreads();
+  }
+  int run = part[t] - c;  // exclusive prefix of this chunk
+  for (int i = i0; i < i1; ++i) {
+    prefix[i] = run;
+    run += (tf[i].w != 0.0f);
+  }
+  if (t == nt - 1) prefix[n] = part[t];
+}
+
+cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t s) {
+  k_tf_prefix<<<1, 1024, 0, s>>>(tf, n, prefix);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ brick visibility
+// A brick is invisible when every table entry a sample in it can touch has alpha == 0.
+// The table coordinate is computed with the same FP32 expression as the march
+// (u = raw * scale, clamped), widened by one entry below and two above so that a one-ulp
+// excursion of an interpolated value cannot reach an unchecked entry.
+__global__ void k_brick_visibility(const float2* __restrict__ mm, int nbricks,
+                                   const int* __restrict__ prefix, int ntf, float scale,
+                                   uint8_t* __restrict__ vis) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbricks) return;
+  const float2 m = mm[i];
+  const float top = (float)(ntf - 1);
+  const float ulo = fminf(fmaxf(m.x * scale, 0.0f), top);
+  const float uhi = fminf(fmaxf(m.y * scale, 0.0f), top);
+  const int jlo = max((int)ulo - 1, 0);
+  const int jhi = min((int)uhi + 2, ntf - 1);
+  vis[i] = (prefix[jhi + 1] - prefix[jlo]) > 0 ? 1 : 0;
+}
+
+cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
+                                    int ntf, float scale, uint8_t* vis, cudaStream_t s) {
+  const int nbricks = nb[0] * nb[1] * nb[2];
+  const int threads = 256;
+  k_brick_visibility<<<(nbricks + threads - 1) / threads, threads, 0, s>>>(mm, nbricks, prefix,
+                                                                          ntf, scale, vis);
+  return cudaGetLastError();
+}
+
+}  // namespace vr

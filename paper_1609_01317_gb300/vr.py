@@ -1,0 +1,192 @@
+"""Thin ctypes binding of ``libvr.so`` (the C ABI in ``include/vr.h``).
+
+Argument marshalling only: every step of the ray march runs in the CUDA kernels of the
+library.  Functions keep the C names; each raises ``VrError`` on a non-zero status.
+Loading fails loudly if the library has not been built (``build.py``); there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvr.so")
+
+VR_OK = 0
+STATUS_NAMES = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_OUT_OF_MEMORY", 3: "VR_ERR_CUDA",
+                4: "VR_ERR_UNSUPPORTED", 5: "VR_ERR_TIMEOUT", 6: "VR_ERR_STATE"}
+DTYPES = {"u8": 0, "u16": 1, "f16": 2, "f32": 3}
+GRADS = {"central": 0, "sobel3d": 1, "zucker_hummel": 2}
+
+
+class VrError(RuntimeError):
+    def __init__(self, func, status, detail=""):
+        self.status = status
+        name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{func}: {name}{(' (' + detail + ')') if detail else ''}")
+
+
+class vr_camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3),
+                ("ortho", C.c_int), ("fov_y_deg", C.c_float), ("ortho_height", C.c_float),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class vr_render_params(C.Structure):
+    _fields_ = [("step", C.c_float), ("grad", C.c_int), ("ka", C.c_float), ("kd", C.c_float),
+                ("ks", C.c_float), ("shininess", C.c_float), ("light", C.c_float * 3),
+                ("headlight", C.c_int), ("ert_threshold", C.c_float), ("skip_empty", C.c_int),
+                ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3),
+                ("collect_stats", C.c_int)]
+
+
+class vr_stats(C.Structure):
+    _fields_ = [("rays_hit", C.c_ulonglong), ("samples_plain", C.c_ulonglong),
+                ("samples_visited", C.c_ulonglong), ("samples_shaded", C.c_ulonglong)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("vr_create", C.c_int, [C.POINTER(C.c_void_p), C.c_int, ALLOC_FN, FREE_FN, C.c_void_p]),
+    ("vr_destroy", None, [C.c_void_p]),
+    ("vr_upload_volume", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.c_float, C.c_void_p]),
+    ("vr_set_transfer_function", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("vr_set_camera", C.c_int, [C.c_void_p, C.POINTER(vr_camera)]),
+    ("vr_render", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p, C.c_void_p]),
+    ("vr_checkpoint_bytes", C.c_int, [C.c_void_p, C.POINTER(vr_render_params),
+                                      C.POINTER(C.c_size_t)]),
+    ("vr_render_forward_train", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p,
+                                          C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("vr_render_backward", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("vr_read_stats", C.c_int, [C.c_void_p, C.POINTER(vr_stats), C.c_void_p]),
+    ("vr_status_string", C.c_char_p, [C.c_int]),
+    ("vr_last_cuda_error", C.c_char_p, []),
+    ("vr_version", C.c_int, []),
+]
+
+_lib = None
+
+
+def lib():
+    """Load libvr.so (raises if it is missing: build it with ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1609_01317_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(func, status):
+    if status != VR_OK:
+        detail = ""
+        if status == 3:
+            detail = lib().vr_last_cuda_error().decode()
+        raise VrError(func, status, detail)
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def make_camera(cam: dict) -> vr_camera:
+    return vr_camera((C.c_float * 3)(*cam["eye"]), (C.c_float * 3)(*cam["target"]),
+                     (C.c_float * 3)(*cam["up"]), int(bool(cam["ortho"])),
+                     float(cam["fov_y_deg"]), float(cam["ortho_height"]), int(cam["width"]),
+                     int(cam["height"]))
+
+
+def make_params(step=0.5, grad="central", ka=0.1, kd=0.7, ks=0.2, shininess=20.0,
+                light=(0.0, 0.0, 0.0), headlight=True, ert_threshold=0.99, skip_empty=True,
+                clip_lo=(-1e30, -1e30, -1e30), clip_hi=(1e30, 1e30, 1e30),
+                collect_stats=False) -> vr_render_params:
+    g = GRADS[grad] if isinstance(grad, str) else int(grad)
+    return vr_render_params(float(step), g, float(ka), float(kd), float(ks), float(shininess),
+                            (C.c_float * 3)(*light), int(bool(headlight)), float(ert_threshold),
+                            int(bool(skip_empty)), (C.c_float * 3)(*clip_lo),
+                            (C.c_float * 3)(*clip_hi), int(bool(collect_stats)))
+
+
+# ----------------------------------------------------------- same-name wrappers
+def vr_create(device=0, alloc=None, free=None, user=None):
+    h = C.c_void_p()
+    a = alloc if alloc is not None else ALLOC_FN()
+    f = free if free is not None else FREE_FN()
+    _check("vr_create", lib().vr_create(C.byref(h), int(device), a, f, user))
+    return h.value
+
+
+def vr_destroy(ctx):
+    lib().vr_destroy(ctx)
+
+
+def vr_upload_volume(ctx, voxels, dtype, nx, ny, nz, value_max, stream=None):
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check("vr_upload_volume", lib().vr_upload_volume(ctx, _ptr(voxels), dt, int(nx), int(ny),
+                                                      int(nz), float(value_max), stream))
+
+
+def vr_set_transfer_function(ctx, rgba, n, stream=None):
+    _check("vr_set_transfer_function", lib().vr_set_transfer_function(ctx, _ptr(rgba), int(n),
+                                                                      stream))
+
+
+def vr_set_camera(ctx, cam):
+    c = cam if isinstance(cam, vr_camera) else make_camera(cam)
+    _check("vr_set_camera", lib().vr_set_camera(ctx, C.byref(c)))
+
+
+def vr_render(ctx, params, out_rgba, stream=None):
+    _check("vr_render", lib().vr_render(ctx, C.byref(params), _ptr(out_rgba), stream))
+
+
+def vr_checkpoint_bytes(ctx, params) -> int:
+    n = C.c_size_t()
+    _check("vr_checkpoint_bytes", lib().vr_checkpoint_bytes(ctx, C.byref(params), C.byref(n)))
+    return n.value
+
+
+def vr_render_forward_train(ctx, params, out_rgba, checkpoints, checkpoint_bytes, stream=None):
+    _check("vr_render_forward_train",
+           lib().vr_render_forward_train(ctx, C.byref(params), _ptr(out_rgba), _ptr(checkpoints),
+                                         int(checkpoint_bytes), stream))
+
+
+def vr_render_backward(ctx, params, checkpoints, grad_rgba, grad_volume, grad_tf, stream=None):
+    _check("vr_render_backward",
+           lib().vr_render_backward(ctx, C.byref(params), _ptr(checkpoints), _ptr(grad_rgba),
+                                    _ptr(grad_volume), _ptr(grad_tf), stream))
+
+
+def vr_read_stats(ctx, stream=None) -> dict:
+    s = vr_stats()
+    _check("vr_read_stats", lib().vr_read_stats(ctx, C.byref(s), stream))
+    return {k: getattr(s, k) for k, _ in vr_stats._fields_}
+
+
+def vr_status_string(status) -> str:
+    return lib().vr_status_string(int(status)).decode()
+
+
+def vr_version() -> int:
+    return lib().vr_version()

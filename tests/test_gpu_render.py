@@ -1,0 +1,234 @@
+"""GPU parity of the forward ray march (vr_render) against the FP64 oracle.
+
+Images must match within 2e-3 max abs per RGBA channel on >= 99.9% of pixels and within
+2e-2 on every pixel (normalised units).  Sample counts come from the kernel's counters
+and are compared with the oracle's per-ray counts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import phantoms as P
+from _util import assert_image_parity, image_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    from paper_1609_01317_gb300 import Renderer, build
+
+    build.build()
+    r = Renderer(0)
+    yield r
+    torch.cuda.synchronize()
+    r.close()
+
+
+def gpu_render(R, vol, vmax, tf, cam, dtype=None, **kw):
+    import torch
+
+    R.upload_volume(vol, vmax, dtype)
+    R.set_transfer_function(tf)
+    R.set_camera(cam)
+    img = R.render(collect_stats=True, **kw)
+    torch.cuda.synchronize()
+    return img.cpu().numpy().astype(np.float64), R.stats()
+
+
+def oracle_render(vol, vmax, tf, cam, **kw):
+    kw = dict(kw)
+    kw.pop("skip_empty", None)
+    kw.pop("collect_stats", None)
+    pr = oracle.make_params(**kw)
+    img, counts, total = oracle.render(oracle.OracleVolume(vol, vmax), tf, cam, pr)
+    return img, counts, total
+
+
+def test_sphere_64_ortho_central(R):
+    w = P.workload_sphere_64()
+    kw = dict(step=0.5, grad="central", skip_empty=False)
+    img, st = gpu_render(R, w["volume"], 255.0, w["tf"], w["camera"], **kw)
+    ref, counts, total = oracle_render(w["volume"], 255.0, w["tf"], w["camera"], **kw)
+    assert_image_parity(img, ref, "sphere64")
+    # axis-aligned rays sit on exact binary fractions: the counts agree exactly
+    assert st["rays_hit"] == 252 * 252
+    assert st["samples_plain"] == total == 252 * 252 * 126
+    assert st["samples_visited"] == total
+
+
+@pytest.mark.parametrize("skip", [False, True])
+def test_ellipsoids_perspective_sobel(R, skip):
+    shp = (64, 64, 64)
+    vol = P.ellipsoids(1, shp)
+    tf = P.tf_two_plateau(256)
+    cam = P.orbit_camera(shp, 128, 112, 0.8, 0.3, 40.0)
+    kw = dict(step=0.5, grad="sobel3d", skip_empty=skip)
+    img, st = gpu_render(R, vol, 4095.0, tf, cam, **kw)
+    ref, counts, total = oracle_render(vol, 4095.0, tf, cam, **kw)
+    assert_image_parity(img, ref, f"ellipsoids skip={skip}")
+    assert abs(st["samples_plain"] - total) <= 1e-4 * total + 8
+    assert st["rays_hit"] == int((counts > 0).sum()) or abs(st["rays_hit"] - (counts > 0).sum()) <= 4
+    if skip:
+        assert st["samples_visited"] < st["samples_plain"]
+
+
+@pytest.mark.parametrize("dtype", ["u16", "f16"])
+def test_ct_phantom_small_zucker_hummel(R, dtype):
+    shp = (96, 96, 68)
+    vol = P.ct_phantom(2, shp)
+    tf = P.tf_two_plateau(256, soft=(900.0, 1300.0))
+    cam = P.orbit_camera(shp, 192, 108, 0.6, 0.35, 40.0)
+    kw = dict(step=0.5, grad="zucker_hummel", skip_empty=True)
+    if dtype == "f16":
+        vol_in = (vol.astype(np.float32) / 4095.0).astype(np.float16)
+        vmax = 1.0
+    else:
+        vol_in, vmax = vol, 4095.0
+    img, st = gpu_render(R, vol_in, vmax, tf, cam, **kw)
+    ref, counts, total = oracle_render(vol_in, vmax, tf, cam, **kw)
+    frac, emax = assert_image_parity(img, ref, f"ct {dtype}")
+    print(f"ct {dtype}: {100 * frac:.4f}% within 2e-3, max {emax:.2e}")
+    assert abs(st["samples_plain"] - total) <= 1e-4 * total + 8
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f16", "f32"])
+@pytest.mark.parametrize("op", ["central", "sobel3d", "zucker_hummel"])
+def test_dtypes_and_operators_ragged_volume(R, dtype, op):
+    """Ragged (non-multiple-of-8) sizes, every storage type and operator."""
+    shp = (21, 13, 17)
+    vmax = {"u8": 255.0, "u16": 4095.0, "f16": 1.0, "f32": 1.0}[dtype]
+    npdt = {"u8": np.uint8, "u16": np.uint16, "f16": np.float16, "f32": np.float32}[dtype]
+    vol = P.ellipsoids(5, shp, count=4, value_max=vmax if dtype in ("u8", "u16") else 4095.0)
+    if dtype in ("f16", "f32"):
+        vol = (vol.astype(np.float64) / 4095.0).astype(npdt)
+    else:
+        vol = vol.astype(npdt)
+    tf = P.tf_random(7, 64, alpha_max=0.25, zero_below=4)
+    cam = P.orbit_camera(shp, 40, 33, 2.3, -0.5, 40.0, radius_diag=1.4)
+    kw = dict(step=0.7, grad=op, skip_empty=True, ert_threshold=0.97)
+    img, st = gpu_render(R, vol, vmax, tf, cam, **kw)
+    ref, counts, total = oracle_render(vol, vmax, tf, cam, **kw)
+    assert_image_parity(img, ref, f"{dtype}/{op}")
+
+
+def test_empty_space_skipping_never_changes_the_image(R):
+    shp = (80, 72, 64)
+    vol = P.ellipsoids(3, shp)
+    tf = P.tf_two_plateau(256)
+    for i, (az, el) in enumerate([(0.1, 0.2), (1.9, -0.7), (4.0, 1.0)]):
+        cam = P.orbit_camera(shp, 96, 80, az, el, 40.0, radius_diag=0.9 + 0.5 * i)
+        a, sa = gpu_render(R, vol, 4095.0, tf, cam, grad="zucker_hummel", skip_empty=False)
+        b, sb = gpu_render(R, vol, 4095.0, tf, cam, grad="zucker_hummel", skip_empty=True)
+        assert np.array_equal(a, b)
+        assert sa["samples_plain"] == sb["samples_plain"]
+        assert sb["samples_visited"] <= sa["samples_visited"]
+
+
+def test_edge_cases(R):
+    import torch
+
+    # all-zero volume with alpha 0 at zero: transparent black everywhere
+    vol = np.zeros((9, 10, 11), np.uint8)
+    tf = P.tf_c1(256)
+    cam = P.orbit_camera((11, 10, 9), 17, 19, 0.3, 0.2, 40.0)
+    img, st = gpu_render(R, vol, 255.0, tf, cam)
+    assert np.all(img == 0.0) and st["samples_shaded"] == 0
+    # camera looking away: every ray misses
+    away = dict(cam)
+    away["target"] = [2 * away["eye"][i] - away["target"][i] for i in range(3)]
+    img, st = gpu_render(R, vol, 255.0, tf, away)
+    assert np.all(img == 0.0) and st["rays_hit"] == 0
+    # 1x1x1, 2x2x2 and a single slice
+    for shp in ((1, 1, 1), (2, 2, 2), (7, 5, 1)):
+        v = P.random_volume(9, shp, np.uint8, 255.0)
+        t = P.tf_random(10, 16, alpha_max=0.5)
+        ctr = P.volume_centre(shp)
+        c = P.camera([ctr[0] + 3.0, ctr[1] + 2.5, ctr[2] + 4.0], ctr, [0, 1, 0], 9, 7)
+        img, _ = gpu_render(R, v, 255.0, t, c, grad="sobel3d")
+        ref, _, _ = oracle_render(v, 255.0, t, c, grad="sobel3d")
+        assert_image_parity(img, ref, f"tiny {shp}")
+    # empty clip box: black
+    v = P.random_volume(11, (12, 12, 12), np.uint16, 4095.0)
+    t = P.tf_random(12, 32, alpha_max=0.3)
+    c = P.orbit_camera((12, 12, 12), 16, 16, 0.5, 0.5, 40.0)
+    img, st = gpu_render(R, v, 4095.0, t, c, clip_lo=(6, 0, 0), clip_hi=(5, 11, 11))
+    assert np.all(img == 0.0)
+    # a clip box that cuts the volume open; a point light; no early termination
+    kw = dict(grad="zucker_hummel", clip_lo=(2.5, 1.0, 0.0), clip_hi=(9.0, 11.0, 7.25),
+              headlight=False, light=(-1000.0, -1000.0, -1000.0), ert_threshold=2.0)
+    img, _ = gpu_render(R, v, 4095.0, t, c, **kw)
+    ref, _, _ = oracle_render(v, 4095.0, t, c, **kw)
+    assert_image_parity(img, ref, "clip + point light")
+    # host output buffer (copied back on the stream)
+    R.upload_volume(v, 4095.0)
+    R.set_transfer_function(t)
+    R.set_camera(c)
+    out = torch.empty((16, 16, 4), dtype=torch.float32).pin_memory()
+    from paper_1609_01317_gb300 import vr
+
+    vr.vr_render(R.ctx, vr.make_params(), out, None)
+    torch.cuda.synchronize()
+    dev = R.render().cpu()
+    torch.cuda.synchronize()
+    assert torch.equal(out, dev)
+
+
+def test_invalid_arguments_and_state(R):
+    import torch
+    from paper_1609_01317_gb300 import vr
+
+    fresh = vr.vr_create(0)
+    try:
+        out = torch.empty((4, 4, 4), device="cuda")
+        with pytest.raises(vr.VrError) as e:
+            vr.vr_render(fresh, vr.make_params(), out)
+        assert e.value.status == 6  # no volume / TF / camera yet
+        with pytest.raises(vr.VrError):
+            vr.vr_upload_volume(fresh, out, "u8", 0, 4, 4, 255.0)
+        with pytest.raises(vr.VrError):
+            vr.vr_upload_volume(fresh, out, "u8", 4, 4, 4, -1.0)
+        with pytest.raises(vr.VrError):
+            vr.vr_set_transfer_function(fresh, out, 1)
+        bad = P.camera([0, 0, 0], [0, 0, 0], [0, 1, 0], 4, 4)
+        with pytest.raises(vr.VrError):
+            vr.vr_set_camera(fresh, bad)
+        bad = P.camera([0, 0, 5], [0, 0, 0], [0, 0, 1], 4, 4)  # up parallel to view
+        with pytest.raises(vr.VrError):
+            vr.vr_set_camera(fresh, bad)
+        bad = P.camera([0, 0, 5], [0, 0, 0], [0, 1, 0], 4, 4, fov_y_deg=180.0)
+        with pytest.raises(vr.VrError):
+            vr.vr_set_camera(fresh, bad)
+        for p in (vr.make_params(step=0.0), vr.make_params(ert_threshold=0.0),
+                  vr.make_params(grad=7), vr.make_params(shininess=-1.0)):
+            with pytest.raises(vr.VrError) as e:
+                vr.vr_render(fresh, p, out)
+            assert e.value.status == 1
+    finally:
+        vr.vr_destroy(fresh)
+
+
+def test_full_size_ct_sampled_pixels(R):
+    """512x512x361 uint16 phantom at 1920x1080 (the benchmark's launch): sampled pixels
+    against the oracle, plus the sample count of those rays."""
+    import torch
+
+    w = P.workload_ct()
+    vol, tf, cam = w["volume"], w["tf"], w["camera"]
+    kw = dict(step=0.5, grad="zucker_hummel", skip_empty=True)
+    img, st = gpu_render(R, vol, 4095.0, tf, cam, **kw)
+    hit = np.argwhere(img[..., 3] > 0)
+    assert len(hit) > 50000
+    rng = np.random.default_rng(5)
+    pick = hit[rng.choice(len(hit), 1500, replace=False)]
+    edge = rng.integers(0, [cam["height"], cam["width"]], size=(300, 2))
+    pick = np.concatenate([pick, edge])
+    pr = oracle.make_params(step=0.5, grad="zucker_hummel")
+    ref, counts, _ = oracle.render_pixels(oracle.OracleVolume(vol, 4095.0), tf, cam, pr,
+                                          pick[:, 1], pick[:, 0])
+    got = img[pick[:, 0], pick[:, 1]]
+    assert_image_parity(got, ref, "ct full size, sampled")
+    torch.cuda.synchronize()
