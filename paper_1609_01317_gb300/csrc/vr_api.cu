@@ -207,10 +207,49 @@ static vr_status refresh_visibility(vr_ctx* ctx, cudaStream_t s) {
                               ctx->brick_vis, s));
 }
 
+// Operator gradient records for the current volume, operator and (with skipping) the
+// current brick visibility; recomputed only when one of them changed.
+static vr_status ensure_records(vr_ctx* ctx, const vr_render_params* p, cudaStream_t s) {
+  const bool skip = p->skip_empty != 0;
+  if (ctx->rec_valid && ctx->rec_vol_gen == ctx->vol_gen && ctx->rec_op == p->grad &&
+      (ctx->rec_all || (skip && ctx->rec_tf_gen == ctx->tf_gen)))
+    return VR_OK;
+  const size_t nvox = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+  void* r = ctx->rec;
+  vr_status st = ensure(ctx, &r, &ctx->rec_cap, nvox * sizeof(float4));
+  if (st != VR_OK) return st;
+  ctx->rec = static_cast<float4*>(r);
+  st = cuda_status(launch_records(vol_dev(ctx), (int)ctx->dtype, p->grad,
+                                  skip ? ctx->brick_vis : nullptr, ctx->rec, s));
+  if (st != VR_OK) {
+    ctx->rec_valid = false;
+    return st;
+  }
+  ctx->rec_valid = true;
+  ctx->rec_all = !skip;
+  ctx->rec_vol_gen = ctx->vol_gen;
+  ctx->rec_tf_gen = ctx->tf_gen;
+  ctx->rec_op = p->grad;
+  return VR_OK;
+}
+
+RecDev rec_dev(const vr_ctx* ctx) {
+  RecDev R;
+  R.rec = ctx->rec;
+  for (int a = 0; a < 3; ++a) R.n[a] = ctx->n[a];
+  R.sx = ctx->n[0] > 1 ? 1 : 0;
+  R.sy = ctx->n[1] > 1 ? ctx->n[0] : 0;
+  R.sz = ctx->n[2] > 1 ? ctx->n[0] * ctx->n[1] : 0;
+  return R;
+}
+
 static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* out,
                                int* ck_kend, float* ck_T, int nslots, cudaStream_t s) {
+  vr_status rst = ensure_records(ctx, p, s);
+  if (rst != VR_OK) return rst;
   MarchLaunch L;
   L.V = vol_dev(ctx);
+  L.R = rec_dev(ctx);
   L.tf = tf_dev(ctx);
   L.cam = ctx->camdev;
   L.r = render_dev(ctx, p);
@@ -218,6 +257,7 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
   L.op = p->grad;
   L.out = reinterpret_cast<float4*>(out);
   L.stats = nullptr;
+  L.tile_counter = reinterpret_cast<unsigned*>(ctx->stats + 4);
   L.ck_kend = ck_kend;
   L.ck_T = ck_T;
   L.nslots = nslots;
@@ -267,7 +307,7 @@ vr_status vr_create(vr_ctx** out, int device, vr_alloc_fn alloc, vr_free_fn free
     return cuda_status(cudaGetLastError());
   }
   void* st = nullptr;
-  const vr_status s = ctx_alloc(ctx, &st, 4 * sizeof(unsigned long long));
+  const vr_status s = ctx_alloc(ctx, &st, 8 * sizeof(unsigned long long));
   if (s != VR_OK) {
     delete ctx;
     return s;
@@ -288,6 +328,7 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->stats);
   ctx_free(ctx, ctx->out_staging);
   ctx_free(ctx, ctx->adj);
+  ctx_free(ctx, ctx->rec);
   delete ctx;
 }
 

@@ -40,6 +40,15 @@ struct VolDev {
   const uint8_t* vis;  // per-brick visibility (1 = some sample may be non-transparent)
 };
 
+// Gradient records over the unpadded grid: rec[x + nx*(y + ny*z)] = (G_x, G_y, G_z, V).
+// sx, sy, sz: element strides to the +1 neighbour (0 along an axis of size 1, where the
+// clamp-to-edge neighbour is the voxel itself).
+struct RecDev {
+  const float4* rec;
+  int n[3];
+  int sx, sy, sz;
+};
+
 struct TfDev {
   const float4* tf;
   int n;
@@ -314,379 +323,6 @@ __device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& 
       ey1[a] = w1 * ydt[a] + w2 * ydu[a];
       ez0[a] = w0 * ytd[a] + w1 * yud[a];
       ez1[a] = w1 * ytd[a] + w2 * yud[a];
-    }
-    g[0] = kD(ex[0], ex[1], ex[2], ex[3], fx);
-    g[1] = kT(ey0[0], ey0[1], ey0[2], ey0[3], fx) + kU(ey1[0], ey1[1], ey1[2], ey1[3], fx);
-    g[2] = kT(ez0[0], ez0[1], ez0[2], ez0[3], fx) + kU(ez1[0], ez1[1], ez1[2], ez1[3], fx);
-  }
-}
-
-// ----------------------------------------------- per-ray neighbourhood cache (§3.5)
-// Along a ray every cell coordinate moves monotonically in the direction of travel, so
-// consecutive samples share most of their 4x4x4 neighbourhood.  The neighbourhood is
-// kept in registers in "travel order" (index 0 is the voxel behind the cell along the
-// ray's direction on that axis, 3 the one ahead); when the cell advances by one on an
-// axis, the cache shifts by one and only the new face is loaded.  In travel order the
-// interpolation kernels keep their form with f' = f (forward axis) or 1 - f (backward
-// axis); the difference kernel D changes sign on a backward axis.
-//
-// Central differences need only the cross-shaped subset of the neighbourhood: the
-// entries with at most one index on the outer layer {0, 3}.
-template <int OP>
-__host__ __device__ constexpr bool hood_needed(int a, int b, int c) {
-  return OP != OP_CENTRAL ||
-         ((a == 0 || a == 3) + (b == 0 || b == 3) + (c == 0 || c == 3)) <= 1;
-}
-
-struct Hood {
-  float N[4][4][4];
-  int ci[3];     // cached cell (travel order irrelevant), ci[0] = INT_MIN: empty
-  int off[3][4]; // element offsets of travel-order index i on each axis
-};
-
-__device__ __forceinline__ void hood_init(Hood& h, const VolDev& V, const float d[3]) {
-  const int pitch[3] = {1, V.px, V.pxy};
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) h.off[a][i] = (d[a] >= 0.0f ? i - 1 : 2 - i) * pitch[a];
-  h.ci[0] = h.ci[1] = h.ci[2] = -0x40000000;
-}
-
-__device__ __forceinline__ bool hood_in_set_rt(int op, int a, int b, int c) {
-  return op != OP_CENTRAL ||
-         ((a == 0 || a == 3) + (b == 0 || b == 3) + (c == 0 || c == 3)) <= 1;
-}
-
-// Bring the cache to cell c (base = padded offset of the cell's voxel).  A move of one
-// cell per axis (in the direction of travel) shifts the cache: after the shifts entry
-// (i,j,k) holds the old entry (i+mx, j+my, k+mz); every needed entry whose source lies
-// outside the cache or outside the needed set is then reloaded.  Larger moves (after a
-// skip) reload everything.
-template <int VTYPE, int OP>
-__device__ __forceinline__ void hood_update(Hood& h, const VolDev& V, const Cell& c,
-                                            const float d[3]) {
-  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
-  int mv[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) mv[a] = d[a] >= 0.0f ? c.ib[a] - h.ci[a] : h.ci[a] - c.ib[a];
-  if ((mv[0] | mv[1] | mv[2]) == 0) return;
-  const bool shift = (unsigned)mv[0] <= 1u && (unsigned)mv[1] <= 1u && (unsigned)mv[2] <= 1u;
-  const int b = c.base;
-  if (!shift) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (hood_needed<OP>(i, j, k))
-            h.N[i][j][k] = ldv<VTYPE>(v, b + h.off[0][i] + h.off[1][j] + h.off[2][k]);
-  } else {
-    if (mv[0]) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) h.N[i][j][k] = h.N[i + 1][j][k];
-    }
-    if (mv[1]) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) h.N[i][j][k] = h.N[i][j + 1][k];
-    }
-    if (mv[2]) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) h.N[i][j][k] = h.N[i][j][k + 1];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (!hood_needed<OP>(i, j, k)) continue;
-          const int si = i + mv[0], sj = j + mv[1], sk = k + mv[2];
-          const bool src_ok = si <= 3 && sj <= 3 && sk <= 3 && hood_in_set_rt(OP, si, sj, sk);
-          if (!src_ok) h.N[i][j][k] = ldv<VTYPE>(v, b + h.off[0][i] + h.off[1][j] + h.off[2][k]);
-        }
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) h.ci[a] = c.ib[a];
-}
-
-// Travel-order fractions.
-__device__ __forceinline__ void hood_frac(const Cell& c, const float d[3], float fp[3]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) fp[a] = d[a] >= 0.0f ? c.f[a] : 1.0f - c.f[a];
-}
-
-// Trilinear value from the cache (inner 2x2x2, x then y then z).
-__device__ __forceinline__ float hood_value(const Hood& h, const float fp[3]) {
-  const float x00 = lerpf(h.N[1][1][1], h.N[2][1][1], fp[0]);
-  const float x10 = lerpf(h.N[1][2][1], h.N[2][2][1], fp[0]);
-  const float x01 = lerpf(h.N[1][1][2], h.N[2][1][2], fp[0]);
-  const float x11 = lerpf(h.N[1][2][2], h.N[2][2][2], fp[0]);
-  const float y0 = lerpf(x00, x10, fp[1]), y1 = lerpf(x01, x11, fp[1]);
-  return lerpf(y0, y1, fp[2]);
-}
-
-// Unscaled operator gradient from the cache (world axes; see value_and_gradient for the
-// contraction scheme).
-template <int OP>
-__device__ __forceinline__ void hood_gradient(const Hood& h, const float fp[3], const float d[3],
-                                              float g[3]) {
-  const float fx = fp[0], fy = fp[1], fz = fp[2];
-  if constexpr (OP == OP_CENTRAL) {
-    float yt[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float z1 = kT(0.f, h.N[a][1][1], h.N[a][1][2], 0.f, fz);
-      const float z2 = kT(0.f, h.N[a][2][1], h.N[a][2][2], 0.f, fz);
-      yt[a] = fmaf(fy, z2 - z1, z1);
-    }
-    g[0] = kD(yt[0], yt[1], yt[2], yt[3], fx);
-    float yd[2];
-#pragma unroll
-    for (int a = 1; a <= 2; ++a) {
-      float zt[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) zt[b] = kT(0.f, h.N[a][b][1], h.N[a][b][2], 0.f, fz);
-      yd[a - 1] = kD(zt[0], zt[1], zt[2], zt[3], fy);
-    }
-    g[1] = fmaf(fx, yd[1] - yd[0], yd[0]);
-    float zd[2][2];
-#pragma unroll
-    for (int a = 1; a <= 2; ++a)
-#pragma unroll
-      for (int b = 1; b <= 2; ++b)
-        zd[a - 1][b - 1] = kD(h.N[a][b][0], h.N[a][b][1], h.N[a][b][2], h.N[a][b][3], fz);
-    const float z0 = fmaf(fy, zd[0][1] - zd[0][0], zd[0][0]);
-    const float z1 = fmaf(fy, zd[1][1] - zd[1][0], zd[1][0]);
-    g[2] = fmaf(fx, z1 - z0, z0);
-  } else {
-    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
-    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
-    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
-    float ex[4], ey0[4], ey1[4], ez0[4], ez1[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      float zt[4], zu[4], zd[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float n0 = h.N[a][b][0], n1 = h.N[a][b][1], n2 = h.N[a][b][2], n3 = h.N[a][b][3];
-        zt[b] = kT(n0, n1, n2, n3, fz);
-        zu[b] = kU(n0, n1, n2, n3, fz);
-        zd[b] = kD(n0, n1, n2, n3, fz);
-      }
-      const float ytt = kT(zt[0], zt[1], zt[2], zt[3], fy);
-      const float yut = kU(zt[0], zt[1], zt[2], zt[3], fy);
-      const float ydt = kD(zt[0], zt[1], zt[2], zt[3], fy);
-      const float ytu = kT(zu[0], zu[1], zu[2], zu[3], fy);
-      const float yuu = kU(zu[0], zu[1], zu[2], zu[3], fy);
-      const float ydu = kD(zu[0], zu[1], zu[2], zu[3], fy);
-      const float ytd = kT(zd[0], zd[1], zd[2], zd[3], fy);
-      const float yud = kU(zd[0], zd[1], zd[2], zd[3], fy);
-      ex[a] = w0 * ytt + w1 * (ytu + yut) + w2 * yuu;
-      ey0[a] = w0 * ydt + w1 * ydu;
-      ey1[a] = w1 * ydt + w2 * ydu;
-      ez0[a] = w0 * ytd + w1 * yud;
-      ez1[a] = w1 * ytd + w2 * yud;
-    }
-    g[0] = kD(ex[0], ex[1], ex[2], ex[3], fx);
-    g[1] = kT(ey0[0], ey0[1], ey0[2], ey0[3], fx) + kU(ey1[0], ey1[1], ey1[2], ey1[3], fx);
-    g[2] = kT(ez0[0], ez0[1], ez0[2], ez0[3], fx) + kU(ez1[0], ez1[1], ez1[2], ez1[3], fx);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) g[a] = d[a] >= 0.0f ? g[a] : -g[a];
-}
-
-// ------------------------------------------- per-ray neighbourhood ring buffer (§3.5)
-// Consecutive samples of a ray share most of their 4x4x4 neighbourhood.  Each thread
-// keeps its ray's neighbourhood in shared memory as a ring indexed by voxel coordinate
-// mod 4: voxel (X, Y, Z) lives in column (X & 3, Y & 3), lane (Z & 3) of a float4.  When
-// the cell advances by one voxel on an axis, the voxels leaving the neighbourhood occupy
-// exactly the slots of the ones entering it, so an advance only loads the new face; a
-// larger jump (after a skip) reloads the whole neighbourhood.  Columns are read as float4
-// in slot order; the z kernels are rotated to slot order instead of the data.
-//
-// Layout: ring[(xs * 4 + ys) * kRingStride + tid], one float4 per column and thread, so a
-// warp's accesses to the same column are consecutive float4s (no bank conflicts).
-struct Ring {
-  float4* base;  // &ring[tid]
-  int stride;    // threads per block (float4 units between columns)
-  int ci[3];     // cached cell, ci[0] = INT_MIN when empty
-};
-
-__device__ __forceinline__ float4& ring_col(const Ring& r, int xs, int ys) {
-  return r.base[(xs * 4 + ys) * r.stride];
-}
-
-// Load the 4 z-voxels of column (X = cell + a - 1, Y = cell + b - 1) in slot order:
-// slot q holds Z = cz - 1 + ((q - rz) & 3) with rz = (cz - 1) & 3.
-template <int VTYPE>
-__device__ __forceinline__ float4 load_column(const typename VoxelT<VTYPE>::T* __restrict__ v,
-                                              int colbase, int rz, int pxy) {
-  float e[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) e[q] = ldv<VTYPE>(v, colbase + (((q - rz) & 3) - 1) * pxy);
-  return make_float4(e[0], e[1], e[2], e[3]);
-}
-
-template <int VTYPE>
-__device__ __forceinline__ void ring_update(Ring& r, const VolDev& V, const Cell& c) {
-  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
-  const int dx = c.ib[0] - r.ci[0], dy = c.ib[1] - r.ci[1], dz = c.ib[2] - r.ci[2];
-  if ((dx | dy | dz) == 0) return;
-  const int px = V.px, pxy = V.pxy;
-  const int rx = (c.ib[0] - 1) & 3, ry = (c.ib[1] - 1) & 3, rz = (c.ib[2] - 1) & 3;
-  const int b0 = c.base - 1 - px;  // offset of (X = cx-1, Y = cy-1, Z = cz)
-  const bool small = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
-  if (!small) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        ring_col(r, (rx + a) & 3, (ry + b) & 3) = load_column<VTYPE>(v, b0 + a + b * px, rz, pxy);
-  } else {
-    if (dx != 0) {
-      const int a = dx > 0 ? 3 : 0;
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        ring_col(r, (rx + a) & 3, (ry + b) & 3) = load_column<VTYPE>(v, b0 + a + b * px, rz, pxy);
-    }
-    if (dy != 0) {
-      const int b = dy > 0 ? 3 : 0;
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-        ring_col(r, (rx + a) & 3, (ry + b) & 3) = load_column<VTYPE>(v, b0 + a + b * px, rz, pxy);
-    }
-    if (dz != 0) {
-      const int cz = dz > 0 ? 3 : 0;
-      const int q = (rz + cz) & 3;
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          float* col = reinterpret_cast<float*>(&ring_col(r, (rx + a) & 3, (ry + b) & 3));
-          col[q] = ldv<VTYPE>(v, b0 + a + b * px + (cz - 1) * pxy);
-        }
-    }
-  }
-  r.ci[0] = c.ib[0];
-  r.ci[1] = c.ib[1];
-  r.ci[2] = c.ib[2];
-}
-
-// 4-tap weights of T, U and D along z, rotated to slot order (slot q <- tap (q - rz) & 3).
-struct ZWeights {
-  float t[4], u[4], d[4];
-};
-
-__device__ __forceinline__ float rot4(float w0, float w1, float w2, float w3, int q, int rz) {
-  const int c = (q - rz) & 3;
-  const float lo = (c & 1) ? w1 : w0, hi = (c & 1) ? w3 : w2;
-  return (c & 2) ? hi : lo;
-}
-
-__device__ __forceinline__ ZWeights z_weights(float fz, int rz) {
-  ZWeights w;
-  const float g = 1.0f - fz;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    w.t[q] = rot4(0.0f, g, fz, 0.0f, q, rz);
-    w.u[q] = rot4(g, fz, g, fz, q, rz);
-    w.d[q] = rot4(-g, -fz, g, fz, q, rz);
-  }
-  return w;
-}
-
-__device__ __forceinline__ float dot4(const float w[4], const float4& x) {
-  return fmaf(w[3], x.w, fmaf(w[2], x.z, fmaf(w[1], x.y, w[0] * x.x)));
-}
-
-// Trilinear value (raw units) from the ring.
-__device__ __forceinline__ float ring_value(const Ring& r, const Cell& c, const ZWeights& zw) {
-  const int rx = (c.ib[0] - 1) & 3, ry = (c.ib[1] - 1) & 3;
-  float zt[2][2];
-#pragma unroll
-  for (int a = 1; a <= 2; ++a)
-#pragma unroll
-    for (int b = 1; b <= 2; ++b) zt[a - 1][b - 1] = dot4(zw.t, ring_col(r, (rx + a) & 3, (ry + b) & 3));
-  const float y0 = lerpf(zt[0][0], zt[0][1], c.f[1]);
-  const float y1 = lerpf(zt[1][0], zt[1][1], c.f[1]);
-  return lerpf(y0, y1, c.f[0]);
-}
-
-// Unscaled operator gradient from the ring (see value_and_gradient for the scheme).
-template <int OP>
-__device__ __forceinline__ void ring_gradient(const Ring& r, const Cell& c, const ZWeights& zw,
-                                              float g[3]) {
-  const int rx = (c.ib[0] - 1) & 3, ry = (c.ib[1] - 1) & 3;
-  const float fx = c.f[0], fy = c.f[1];
-  if constexpr (OP == OP_CENTRAL) {
-    float yt[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float z1 = dot4(zw.t, ring_col(r, (rx + a) & 3, (ry + 1) & 3));
-      const float z2 = dot4(zw.t, ring_col(r, (rx + a) & 3, (ry + 2) & 3));
-      yt[a] = lerpf(z1, z2, fy);
-    }
-    g[0] = kD(yt[0], yt[1], yt[2], yt[3], fx);
-    float yd[2];
-#pragma unroll
-    for (int a = 1; a <= 2; ++a) {
-      float zt[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) zt[b] = dot4(zw.t, ring_col(r, (rx + a) & 3, (ry + b) & 3));
-      yd[a - 1] = kD(zt[0], zt[1], zt[2], zt[3], fy);
-    }
-    g[1] = lerpf(yd[0], yd[1], fx);
-    float zd[2][2];
-#pragma unroll
-    for (int a = 1; a <= 2; ++a)
-#pragma unroll
-      for (int b = 1; b <= 2; ++b)
-        zd[a - 1][b - 1] = dot4(zw.d, ring_col(r, (rx + a) & 3, (ry + b) & 3));
-    const float z0 = lerpf(zd[0][0], zd[0][1], fy);
-    const float z1 = lerpf(zd[1][0], zd[1][1], fy);
-    g[2] = lerpf(z0, z1, fx);
-  } else {
-    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
-    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
-    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
-    float ex[4], ey0[4], ey1[4], ez0[4], ez1[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      float zt[4], zu[4], zd[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float4 col = ring_col(r, (rx + a) & 3, (ry + b) & 3);
-        zt[b] = dot4(zw.t, col);
-        zu[b] = dot4(zw.u, col);
-        zd[b] = dot4(zw.d, col);
-      }
-      const float ytt = kT(zt[0], zt[1], zt[2], zt[3], fy);
-      const float yut = kU(zt[0], zt[1], zt[2], zt[3], fy);
-      const float ydt = kD(zt[0], zt[1], zt[2], zt[3], fy);
-      const float ytu = kT(zu[0], zu[1], zu[2], zu[3], fy);
-      const float yuu = kU(zu[0], zu[1], zu[2], zu[3], fy);
-      const float ydu = kD(zu[0], zu[1], zu[2], zu[3], fy);
-      const float ytd = kT(zd[0], zd[1], zd[2], zd[3], fy);
-      const float yud = kU(zd[0], zd[1], zd[2], zd[3], fy);
-      ex[a] = fmaf(w0, ytt, fmaf(w1, ytu + yut, w2 * yuu));
-      ey0[a] = fmaf(w0, ydt, w1 * ydu);
-      ey1[a] = fmaf(w1, ydt, w2 * ydu);
-      ez0[a] = fmaf(w0, ytd, w1 * yud);
-      ez1[a] = fmaf(w1, ytd, w2 * yud);
     }
     g[0] = kD(ex[0], ex[1], ex[2], ex[3], fx);
     g[1] = kT(ey0[0], ey0[1], ey0[2], ey0[3], fx) + kU(ey1[0], ey1[1], ey1[2], ey1[3], fx);

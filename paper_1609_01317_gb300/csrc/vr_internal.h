@@ -59,7 +59,7 @@ struct vr_ctx {
   vr_camera cam{};
   vr::CamDev camdev{};
 
-  // statistics
+  // statistics (4 counters) followed by the march's tile counter
   unsigned long long* stats = nullptr;
   bool stats_valid = false;
 
@@ -70,6 +70,13 @@ struct vr_ctx {
   // adjoint scratch: per voxel (dL/ds, dL/dG) at the cell corners, float4
   float4* adj = nullptr;
   size_t adj_cap = 0;
+
+  // operator gradient records (G, V) per voxel and what they were computed for
+  float4* rec = nullptr;
+  size_t rec_cap = 0;
+  bool rec_valid = false, rec_all = false;
+  uint64_t rec_vol_gen = 0, rec_tf_gen = 0;
+  int rec_op = -1;
 
   vr::CkptRecord ckpt[vr::kMaxCkptRecords];
   int ckpt_next = 0;
@@ -97,14 +104,19 @@ cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t 
 cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
                                     int ntf, float scale, uint8_t* vis, cudaStream_t s);
 
+cudaError_t launch_records(const VolDev& V, int dtype, int op, const uint8_t* need,
+                           float4* rec, cudaStream_t s);
+
 struct MarchLaunch {
   VolDev V;
+  RecDev R;
   TfDev tf;
   CamDev cam;
   RenderDev r;
   int dtype, op;
   float4* out;
   unsigned long long* stats;  // NULL: no counting
+  unsigned* tile_counter;     // work counter of the persistent launch (zeroed per launch)
   int* ck_kend;               // NULL: no checkpoints
   float* ck_T;
   int nslots;

@@ -211,3 +211,120 @@ cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int
 }
 
 }  // namespace vr
+
+namespace vr {
+
+// ------------------------------------------------------ operator gradient records
+// rec[v] = (G_x, G_y, G_z, V) at every voxel v a sample can use as a cell corner, where
+// G is the integer-grid operator of §3.5 (Eq. 3, Eq. 4, Zucker-Hummel) applied to the
+// clamp-to-edge volume: G_a(v) = sum_o W^a_o E(v + o), unscaled, in raw value units.
+// Because every tap of a sample shares the sample's fractional weights, the operator
+// gradient at any point p equals the trilinear blend of G over p's cell corners, so the
+// march reads 8 records per sample instead of evaluating the taps.
+//
+// A brick needs the records of voxels [8b, 8b+8]^3 (its cells' corners); with skipping
+// on, only visible bricks are visited.  One block per brick: the 11^3 clamp-to-edge
+// neighbourhood [8b-1, 8b+9]^3 is staged in shared memory, then each thread computes
+// records from it.
+template <int VTYPE, int OP>
+__global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* __restrict__ need,
+                                                 float4* __restrict__ rec) {
+  __shared__ float tile[11][11][12];  // [z][y][x], x padded to 12
+  const int bid = blockIdx.x;
+  if (need && !need[bid]) return;
+  const int t = threadIdx.x;
+  const int bx = bid % V.nb[0], by = (bid / V.nb[0]) % V.nb[1], bz = bid / (V.nb[0] * V.nb[1]);
+  const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
+  const int nx = V.n[0], ny = V.n[1], nz = V.n[2];
+  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
+  // stage: thread (i, j) loads the z column of [x0-1+i, y0-1+j]; coordinates beyond n
+  // are clamped to n (still inside the padded border, where E is the edge value)
+  if (t < 121) {
+    const int i = t % 11, j = t / 11;
+    const int X = min(x0 - 1 + i, nx), Y = min(y0 - 1 + j, ny);
+    const int colp = (X + kPadLo) + V.px * (Y + kPadLo);
+#pragma unroll
+    for (int k = 0; k < 11; ++k) {
+      const int Z = min(z0 - 1 + k, nz);
+      tile[k][j][i] = ldv<VTYPE>(v, colp + V.pxy * (Z + kPadLo));
+    }
+  }
+  __syncthreads();
+  if (t >= 81) return;
+  const int u = t % 9, w = t / 9;  // x, y offsets in the brick
+  const int x = x0 + u, y = y0 + w;
+  if (x >= nx || y >= ny) return;
+  constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+  constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+  constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+  float P[3][3][3];  // [z][y][x] neighbourhood of the current voxel, rolled along z
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) P[c][b][a] = tile[c][w + b][u + a];
+  const int qn = min(kBrick + 1, nz - z0);
+  float4* out = rec + (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z0);
+  const size_t zstride = (size_t)nx * ny;
+  for (int q = 0; q < qn; ++q) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) P[2][b][a] = tile[q + 2][w + b][u + a];
+    float g[3];
+    if constexpr (OP == OP_CENTRAL) {
+      g[0] = P[1][1][2] - P[1][1][0];
+      g[1] = P[1][2][1] - P[1][0][1];
+      g[2] = P[2][1][1] - P[0][1][1];
+    } else {
+      float d[3][3][3];  // difference planes along x ([z][y]), y ([z][x]), z ([y][x])
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          d[0][a][b] = P[a][b][2] - P[a][b][0];
+          d[1][a][b] = P[a][2][b] - P[a][0][b];
+          d[2][a][b] = P[2][a][b] - P[0][a][b];
+        }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float edges = (d[c][0][1] + d[c][2][1]) + (d[c][1][0] + d[c][1][2]);
+        const float corners = (d[c][0][0] + d[c][0][2]) + (d[c][2][0] + d[c][2][2]);
+        g[c] = fmaf(w0, d[c][1][1], fmaf(w1, edges, w2 * corners));
+      }
+    }
+    out[q * zstride] = make_float4(g[0], g[1], g[2], P[1][1][1]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        P[0][b][a] = P[1][b][a];
+        P[1][b][a] = P[2][b][a];
+      }
+  }
+}
+
+template <int VTYPE>
+static void launch_records_op(const VolDev& V, int op, const uint8_t* need, float4* rec,
+                              cudaStream_t s) {
+  const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
+  switch (op) {
+    case OP_CENTRAL: k_records<VTYPE, OP_CENTRAL><<<nbricks, 128, 0, s>>>(V, need, rec); break;
+    case OP_SOBEL: k_records<VTYPE, OP_SOBEL><<<nbricks, 128, 0, s>>>(V, need, rec); break;
+    default: k_records<VTYPE, OP_ZH><<<nbricks, 128, 0, s>>>(V, need, rec);
+  }
+}
+
+cudaError_t launch_records(const VolDev& V, int dtype, int op, const uint8_t* need,
+                           float4* rec, cudaStream_t s) {
+  switch (dtype) {
+    case VT_U8: launch_records_op<VT_U8>(V, op, need, rec, s); break;
+    case VT_U16: launch_records_op<VT_U16>(V, op, need, rec, s); break;
+    case VT_F16: launch_records_op<VT_F16>(V, op, need, rec, s); break;
+    default: launch_records_op<VT_F32>(V, op, need, rec, s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace vr
