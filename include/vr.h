@@ -168,6 +168,34 @@ vr_status vr_render_backward(vr_ctx *ctx, const vr_render_params *params,
                              const void *checkpoints, const float *grad_rgba,
                              float *grad_volume, float *grad_tf, void *stream);
 
+/* Render without allocating any device memory.  (The paper has no counterpart: this entry
+ * exists for callers that cannot allocate device memory when they render -- a plug-in
+ * inside an application that owns the device's whole memory pool, a real-time loop that
+ * must not allocate per frame, or a process whose device memory is already reserved by
+ * another framework's caching allocator.)
+ * No context is used: the caller passes, in device memory of the current CUDA device,
+ * the dense volume `voxels` (nx*ny*nz of `dtype`, x fastest, read in place), the
+ * transfer function `tf_rgba` (ntf x 4 float32) and the output `out_rgba` (H x W x 4
+ * float32), plus the camera and the parameters as host structs; the result equals
+ * vr_render's on the same inputs up to FP32 rounding (the operator gradient is evaluated
+ * from each sample's neighbourhood instead of precomputed records).
+ * The library's scratch (brick min/max and visibility tables, transfer-function prefix
+ * counts, the work counter) is a fixed array in device memory that every GPU loading the
+ * library holds until the process exits; its limits are at most 262144 bricks of 8^3
+ * voxels (e.g. 512^3 voxels) and ntf <= 4096 -- larger requests return
+ * VR_ERR_INVALID_ARG.  All calls on a device share that array and each call rewrites it
+ * (the work counter is cleared on `stream` first), so calls whose work overlaps on the
+ * GPU (different streams, or other host threads) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address (host code
+ * cannot use the array's name as a device pointer); make that first call before any
+ * stream capture.  collect_stats must be 0 (VR_ERR_UNSUPPORTED otherwise).
+ * Errors: INVALID_ARG (NULL or host pointers, sizes out of range or beyond the scratch
+ * limits, invalid camera or parameters), UNSUPPORTED, CUDA. */
+vr_status vr_render_noalloc(const void *voxels, vr_dtype dtype, int nx, int ny, int nz,
+                            float value_max, const float *tf_rgba, int ntf,
+                            const vr_camera *cam, const vr_render_params *params,
+                            float *out_rgba, void *stream);
+
 /* Copy the counters of the last render with collect_stats = 1 into *out.  Synchronises
  * `stream`.  Errors: INVALID_ARG, STATE (no such render), CUDA. */
 vr_status vr_read_stats(vr_ctx *ctx, vr_stats *out, void *stream);

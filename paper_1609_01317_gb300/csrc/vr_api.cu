@@ -66,7 +66,7 @@ struct DeviceGuard {
   }
 };
 
-static bool is_device_pointer(const void* p) {
+bool is_device_pointer(const void* p) {
   cudaPointerAttributes a;
   const cudaError_t e = cudaPointerGetAttributes(&a, p);
   if (e != cudaSuccess) {
@@ -113,17 +113,17 @@ TfDev tf_dev(const vr_ctx* ctx) {
   return t;
 }
 
-RenderDev render_dev(const vr_ctx* ctx, const vr_render_params* p) {
+RenderDev render_dev_for(const int n[3], float value_max, const vr_render_params* p) {
   RenderDev r;
   r.step = p->step;
   r.ert = p->ert_threshold;
   r.skip = p->skip_empty ? 1 : 0;
   for (int a = 0; a < 3; ++a) {
-    const float vhi = (float)(ctx->n[a] - 1);
+    const float vhi = (float)(n[a] - 1);
     r.lo[a] = p->clip_lo[a] > 0.0f ? p->clip_lo[a] : 0.0f;
     r.hi[a] = p->clip_hi[a] < vhi ? p->clip_hi[a] : vhi;
   }
-  r.gscale = op_scale(p->grad) / ctx->value_max;
+  r.gscale = op_scale(p->grad) / value_max;
   r.sh.ka = p->ka;
   r.sh.kd = p->kd;
   r.sh.ks = p->ks;
@@ -131,6 +131,10 @@ RenderDev render_dev(const vr_ctx* ctx, const vr_render_params* p) {
   for (int a = 0; a < 3; ++a) r.sh.light[a] = p->light[a];
   r.sh.headlight = p->headlight ? 1 : 0;
   return r;
+}
+
+RenderDev render_dev(const vr_ctx* ctx, const vr_render_params* p) {
+  return render_dev_for(ctx->n, ctx->value_max, p);
 }
 
 // Upper bound of the per-ray sample count K for the current box and step.
@@ -147,7 +151,7 @@ int max_samples(const vr_ctx* ctx, const vr_render_params* p) {
 
 // FP32 camera basis with every operation rounded on its own (this file is compiled with
 // -ffp-contract=off for the host): fwd, right, up' and the screen half-extents.
-static bool camera_basis(const vr_camera* c, CamDev* b) {
+bool camera_basis(const vr_camera* c, CamDev* b) {
   float f[3], r[3], u[3];
   for (int a = 0; a < 3; ++a) f[a] = c->target[a] - c->eye[a];
   float l = f[0] * f[0];
@@ -185,7 +189,7 @@ static bool camera_basis(const vr_camera* c, CamDev* b) {
   return true;
 }
 
-static vr_status check_params(const vr_render_params* p) {
+vr_status check_params(const vr_render_params* p) {
   if (!p) return VR_ERR_INVALID_ARG;
   if (!(p->step > 0.0f) || !std::isfinite(p->step)) return VR_ERR_INVALID_ARG;
   if (p->grad < VR_GRAD_CENTRAL || p->grad > VR_GRAD_ZUCKER_HUMMEL) return VR_ERR_INVALID_ARG;
@@ -281,6 +285,22 @@ static void ckpt_layout(vr_ctx* ctx, const vr_render_params* p, int* nrays, int*
   *bytes = align256((size_t)*nrays * 4) + (size_t)*nrays * 4 * (size_t)*nslots;
 }
 
+}  // namespace vr
+
+namespace vr {
+
+vr_status check_camera(const vr_camera* cam, CamDev* b) {
+  if (!cam) return VR_ERR_INVALID_ARG;
+  if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+    return VR_ERR_INVALID_ARG;
+  if (!finite3(cam->eye) || !finite3(cam->target) || !finite3(cam->up)) return VR_ERR_INVALID_ARG;
+  if (cam->ortho) {
+    if (!(cam->ortho_height > 0.0f) || !std::isfinite(cam->ortho_height)) return VR_ERR_INVALID_ARG;
+  } else {
+    if (!(cam->fov_y_deg > 0.0f && cam->fov_y_deg < 180.0f)) return VR_ERR_INVALID_ARG;
+  }
+  return camera_basis(cam, b) ? VR_OK : VR_ERR_INVALID_ARG;
+}
 }  // namespace vr
 
 using namespace vr;
@@ -421,18 +441,12 @@ vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, void* 
   return st;
 }
 
+
 vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cam) {
   if (!ctx || !cam) return VR_ERR_INVALID_ARG;
-  if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
-    return VR_ERR_INVALID_ARG;
-  if (!finite3(cam->eye) || !finite3(cam->target) || !finite3(cam->up)) return VR_ERR_INVALID_ARG;
-  if (cam->ortho) {
-    if (!(cam->ortho_height > 0.0f) || !std::isfinite(cam->ortho_height)) return VR_ERR_INVALID_ARG;
-  } else {
-    if (!(cam->fov_y_deg > 0.0f && cam->fov_y_deg < 180.0f)) return VR_ERR_INVALID_ARG;
-  }
   CamDev b;
-  if (!camera_basis(cam, &b)) return VR_ERR_INVALID_ARG;
+  const vr_status st = check_camera(cam, &b);
+  if (st != VR_OK) return st;
   ctx->cam = *cam;
   ctx->camdev = b;
   ctx->has_camera = true;

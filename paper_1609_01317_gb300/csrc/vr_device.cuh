@@ -234,14 +234,12 @@ __device__ __forceinline__ float kD(float x0, float x1, float x2, float x3, floa
   return fmaf(f, q - p, p);
 }
 
-// Value (raw units) and unscaled operator gradient from the 4^3 neighbourhood.
-template <int VTYPE, int OP>
-__device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& c, float& s,
-                                                   float g[3]) {
-  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
-  const int px = V.px, pxy = V.pxy;
-  const int b0 = c.base - 1 - px - pxy;  // offset of N[0][0][0]
-  const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
+// Value (raw units) and unscaled operator gradient from the 4^3 neighbourhood, read
+// through nb(a, b, c) = N[a][b][c] = E(i0 + (a-1, b-1, c-1)).
+template <int OP, typename Hood>
+__device__ __forceinline__ void contract_neighbourhood(const Hood& nb, const float f[3], float& s,
+                                                       float g[3]) {
+  const float fx = f[0], fy = f[1], fz = f[2];
   if constexpr (OP == OP_CENTRAL) {
     // Eq. 3 blended over the cell: only the cross-shaped 32-voxel subset is needed.
     // zt[a][b] = T_z-contraction for b in {1,2}; all a.
@@ -250,8 +248,7 @@ __device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 1; b <= 2; ++b) {
-        const int o = b0 + a + b * px;
-        zt_x[a][b - 1] = kT(0.f, ldv<VTYPE>(v, o + pxy), ldv<VTYPE>(v, o + 2 * pxy), 0.f, fz);
+        zt_x[a][b - 1] = kT(0.f, nb(a, b, 1), nb(a, b, 2), 0.f, fz);
       }
 #pragma unroll
     for (int a = 1; a <= 2; ++a)
@@ -260,18 +257,14 @@ __device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& 
         if (b == 1 || b == 2) {
           zt_y[a - 1][b] = zt_x[a][b - 1];
         } else {
-          const int o = b0 + a + b * px;
-          zt_y[a - 1][b] = kT(0.f, ldv<VTYPE>(v, o + pxy), ldv<VTYPE>(v, o + 2 * pxy), 0.f, fz);
+          zt_y[a - 1][b] = kT(0.f, nb(a, b, 1), nb(a, b, 2), 0.f, fz);
         }
       }
 #pragma unroll
     for (int a = 1; a <= 2; ++a)
 #pragma unroll
       for (int b = 1; b <= 2; ++b) {
-        const int o = b0 + a + b * px;
-        const float n0 = ldv<VTYPE>(v, o), n3 = ldv<VTYPE>(v, o + 3 * pxy);
-        const float n1 = ldv<VTYPE>(v, o + pxy), n2 = ldv<VTYPE>(v, o + 2 * pxy);
-        zd[a - 1][b - 1] = kD(n0, n1, n2, n3, fz);
+        zd[a - 1][b - 1] = kD(nb(a, b, 0), nb(a, b, 1), nb(a, b, 2), nb(a, b, 3), fz);
       }
     // x: D_x over a of (T_y over b of zt)
     float yt[4];
@@ -295,9 +288,7 @@ __device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const int o = b0 + a + b * px;
-        const float n0 = ldv<VTYPE>(v, o), n1 = ldv<VTYPE>(v, o + pxy);
-        const float n2 = ldv<VTYPE>(v, o + 2 * pxy), n3 = ldv<VTYPE>(v, o + 3 * pxy);
+        const float n0 = nb(a, b, 0), n1 = nb(a, b, 1), n2 = nb(a, b, 2), n3 = nb(a, b, 3);
         Zt[a][b] = kT(n0, n1, n2, n3, fz);
         Zu[a][b] = kU(n0, n1, n2, n3, fz);
         Zd[a][b] = kD(n0, n1, n2, n3, fz);
@@ -328,6 +319,24 @@ __device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& 
     g[1] = kT(ey0[0], ey0[1], ey0[2], ey0[3], fx) + kU(ey1[0], ey1[1], ey1[2], ey1[3], fx);
     g[2] = kT(ez0[0], ez0[1], ez0[2], ez0[3], fx) + kU(ez1[0], ez1[1], ez1[2], ez1[3], fx);
   }
+}
+
+// Neighbourhood of a cell in the padded volume (no clamping needed).
+template <int VTYPE>
+struct PaddedHood {
+  const typename VoxelT<VTYPE>::T* v;
+  int b0, px, pxy;  // b0: padded offset of N[0][0][0]
+  __device__ __forceinline__ float operator()(int a, int b, int c) const {
+    return ldv<VTYPE>(v, b0 + a + b * px + c * pxy);
+  }
+};
+
+template <int VTYPE, int OP>
+__device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& c, float& s,
+                                                   float g[3]) {
+  PaddedHood<VTYPE> nb{static_cast<const typename VoxelT<VTYPE>::T*>(V.data),
+                       c.base - 1 - V.px - V.pxy, V.px, V.pxy};
+  contract_neighbourhood<OP>(nb, c.f, s, g);
 }
 
 // Scale of each operator: 1 / (2 * sum of one side's weights).

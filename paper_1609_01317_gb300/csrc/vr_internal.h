@@ -90,8 +90,15 @@ void ctx_free(vr_ctx* ctx, void* p);
 vr_status ensure(vr_ctx* ctx, void** p, size_t* cap, size_t bytes);
 vr_status cuda_status(cudaError_t e);
 
+// argument checks and host-side set-up shared by the entry points
+vr_status check_params(const vr_render_params* p);
+vr_status check_camera(const vr_camera* cam, CamDev* basis);
+bool camera_basis(const vr_camera* c, CamDev* b);
+bool is_device_pointer(const void* p);
+
 // device descriptors
 VolDev vol_dev(const vr_ctx* ctx);
+RenderDev render_dev_for(const int n[3], float value_max, const vr_render_params* p);
 TfDev tf_dev(const vr_ctx* ctx);
 RenderDev render_dev(const vr_ctx* ctx, const vr_render_params* p);
 int max_samples(const vr_ctx* ctx, const vr_render_params* p);

@@ -65,6 +65,9 @@ _SIGS = [
     ("vr_render_backward", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("vr_read_stats", C.c_int, [C.c_void_p, C.POINTER(vr_stats), C.c_void_p]),
+    ("vr_render_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
+                                    C.c_void_p, C.c_int, C.POINTER(vr_camera),
+                                    C.POINTER(vr_render_params), C.c_void_p, C.c_void_p]),
     ("vr_status_string", C.c_char_p, [C.c_int]),
     ("vr_last_cuda_error", C.c_char_p, []),
     ("vr_version", C.c_int, []),
@@ -176,6 +179,16 @@ def vr_render_backward(ctx, params, checkpoints, grad_rgba, grad_volume, grad_tf
     _check("vr_render_backward",
            lib().vr_render_backward(ctx, C.byref(params), _ptr(checkpoints), _ptr(grad_rgba),
                                     _ptr(grad_volume), _ptr(grad_tf), stream))
+
+
+def vr_render_noalloc(voxels, dtype, nx, ny, nz, value_max, tf_rgba, ntf, cam, params,
+                      out_rgba, stream=None):
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    c = cam if isinstance(cam, vr_camera) else make_camera(cam)
+    _check("vr_render_noalloc",
+           lib().vr_render_noalloc(_ptr(voxels), dt, int(nx), int(ny), int(nz), float(value_max),
+                                   _ptr(tf_rgba), int(ntf), C.byref(c), C.byref(params),
+                                   _ptr(out_rgba), stream))
 
 
 def vr_read_stats(ctx, stream=None) -> dict:
