@@ -237,6 +237,73 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------ GPU leg
+def fwd_bwd_leg(R, args):
+    """Differentiable workload: 128^3 float32 blurred density, learnable 256-entry TF,
+    16 views at 256x256, central differences, step 0.5.  Times the forward that records
+    adjoint checkpoints against forward + backward (vr_render_backward), Gsamples/s on the
+    same plain-method sample count."""
+    import torch
+
+    import phantoms as P
+    from paper_1609_01317_gb300 import vr
+
+    n = 128
+    vol = torch.from_numpy(P.blurred_random_field(4, n)).cuda()
+    tf = torch.from_numpy(P.tf_c1(256)).cuda()
+    views = P.training_views(n, 256, 256)
+    ctx = R.ctx
+    sh = torch.cuda.current_stream().cuda_stream or None
+    params = vr.make_params(grad="central", skip_empty=False, ert_threshold=0.99)
+    pst = vr.make_params(grad="central", skip_empty=False, ert_threshold=0.99, collect_stats=True)
+    vr.vr_upload_volume(ctx, vol, "f32", n, n, n, 1.0, sh)
+    vr.vr_set_transfer_function(ctx, tf, 256, sh)
+    img = torch.empty((256, 256, 4), device="cuda")
+    gimg = torch.randn((256, 256, 4), device="cuda") * 1e-3
+    gv = torch.zeros_like(vol)
+    gt = torch.zeros_like(tf)
+    cams = [vr.make_camera(c) for c in views]
+    vr.vr_set_camera(ctx, cams[0])
+    nb = vr.vr_checkpoint_bytes(ctx, params) + 256
+    ck = [torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in views]
+    ckv = [(c[(-c.data_ptr()) % 256:]) for c in ck]
+    samples = 0
+    for c in cams:
+        vr.vr_set_camera(ctx, c)
+        vr.vr_render(ctx, pst, img, sh)
+        samples += vr.vr_read_stats(ctx, sh)["samples_plain"]
+
+    def fwd():
+        for i, c in enumerate(cams):
+            vr.vr_set_camera(ctx, c)
+            vr.vr_render_forward_train(ctx, params, img, ckv[i], nb - 256, sh)
+
+    def fwdbwd():
+        for i, c in enumerate(cams):
+            vr.vr_set_camera(ctx, c)
+            vr.vr_render_forward_train(ctx, params, img, ckv[i], nb - 256, sh)
+        vr.vr_render_backward_views(ctx, params, cams, ckv, [gimg] * len(cams), gv, gt, sh)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, min(args.steps, 10))
+    t_f = timed(fwd, reps)
+    t_fb = timed(fwdbwd, reps)
+    return {"workload": "density128_f32_16views256_cd", "samples": samples,
+            "fwd_ms": t_f, "fwd_bwd_ms": t_fb, "ratio": t_fb / t_f,
+            "fwd_gsamples_s": samples / (t_f / 1e3) / 1e9,
+            "fwd_bwd_gsamples_s": samples / (t_fb / 1e3) / 1e9}
+
+
 def run_ours(args):
     import torch
 
@@ -354,6 +421,8 @@ def run_ours(args):
     }
     line["clocks"] = clk.summary()
 
+    if not args.no_extras:
+        line["fwd_bwd"] = fwd_bwd_leg(R, args)
     if not args.no_extras and world == 1:
         # end to end through the C ABI with host buffers: H2D of the volume and TF, D2H of
         # the image, every step

@@ -196,6 +196,18 @@ vr_status vr_render_noalloc(const void *voxels, vr_dtype dtype, int nx, int ny, 
                             const vr_camera *cam, const vr_render_params *params,
                             float *out_rgba, void *stream);
 
+/* vr_render_backward for `nviews` views (1 .. 256) of the current volume and transfer
+ * function in one call: cams[v] is the camera view v was rendered with and checkpoints[v]
+ * / grad_rgba[v] its checkpoint buffer and image gradient.  The gradients of all views
+ * are summed into grad_volume / grad_tf (+=).  Equivalent to nviews vr_render_backward
+ * calls, but the per-voxel accumulator is cleared once and the transposed operator
+ * stencil applied once.  Errors as vr_render_backward; all views are validated before
+ * any work is queued. */
+vr_status vr_render_backward_views(vr_ctx *ctx, const vr_render_params *params, int nviews,
+                                   const vr_camera *cams, const void *const *checkpoints,
+                                   const float *const *grad_rgba, float *grad_volume,
+                                   float *grad_tf, void *stream);
+
 /* Copy the counters of the last render with collect_stats = 1 into *out.  Synchronises
  * `stream`.  Errors: INVALID_ARG, STATE (no such render), CUDA. */
 vr_status vr_read_stats(vr_ctx *ctx, vr_stats *out, void *stream);

@@ -3,9 +3,10 @@
 // The forward pass (vr_render_forward_train) stores, per ray, the index of the last
 // sample it composited and the transmittance T before every 32nd sample.  The adjoint
 // walks each ray back to front one 32-sample segment at a time: it recomputes the
-// segment's transmittances from the stored T (cheap: value + transfer function only),
-// then visits the samples in reverse order, recomputing each sample in full (value,
-// gradient, normal, Phong) and applying the chain rule of Eq. 6 (§3.9):
+// segment's transmittances from the stored T (value + transfer function only), then
+// visits the samples in reverse order, recomputing each sample in full from the gradient
+// records (value, operator gradient, normal, Phong) and applying the chain rule of Eq. 6
+// (§3.9):
 //   C = sum_k T_k a_k c_k,  T_{k+1} = T_k (1 - a_k),  A = 1 - T_end
 //   dL/da_k = T_k (g.c_k - Tadj_{k+1}),  dL/dc_k = T_k a_k g,
 //   Tadj_k  = a_k g.c_k + (1 - a_k) Tadj_{k+1},  Tadj_end = -dL/dA,
@@ -19,177 +20,284 @@
 
 namespace vr {
 
-constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
-constexpr int kMaxSharedTf = 1024;  // tables up to this size accumulate in shared memory
+constexpr int kThreads = 128;
+constexpr int kMaxWarpTf = 512;  // per-warp shared TF tables up to this many entries
+constexpr int kQuadTileW = 4, kQuadTileH = 2;  // pixels per warp (a quad of lanes per ray)
 
-template <int VTYPE>
-__device__ __forceinline__ float alpha_at(const VolDev& V, const TfDev& tf, const float o[3],
-                                          const float d[3], float tn, float step, int k) {
-  const float t = fmaf((float)k + 0.5f, step, tn);
-  float p[3];
+// Corner records of a cell and the trilinear weights of the sample in it.
+struct AdjCell {
+  size_t base;  // record index of the cell's (0,0,0) corner
+  float f[3];
+};
+
+__device__ __forceinline__ AdjCell adj_cell(const VolDev& V, const float p[3]) {
+  AdjCell a;
+  int ib[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
-  const Cell c = cell_of(V, p);
-  return tf_lookup(tf, trilinear<VTYPE>(V, c)).rgba.w;
+  for (int i = 0; i < 3; ++i) {
+    int c = (int)floorf(p[i]);
+    const int top = V.n[i] > 1 ? V.n[i] - 2 : 0;
+    c = c < 0 ? 0 : (c > top ? top : c);
+    ib[i] = c;
+    a.f[i] = p[i] - (float)c;
+  }
+  a.base = (size_t)ib[0] + (size_t)V.n[0] * ((size_t)ib[1] + (size_t)V.n[1] * ib[2]);
+  return a;
 }
 
-template <int VTYPE, int OP>
-__global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
-  extern __shared__ float smem[];
-  float* Ts = smem;                               // [kCkptStride][kThreads]
-  float* hist = smem + kCkptStride * kThreads;    // [ntf][4] when shared
-  const bool shared_tf = L.grad_tf && L.tf.n <= kMaxSharedTf;
-  const int tid = threadIdx.x;
-  if (shared_tf)
-    for (int i = tid; i < 4 * L.tf.n; i += kThreads) hist[i] = 0.0f;
-  __syncthreads();
+__device__ __forceinline__ size_t corner_index(const RecDev& R, size_t base, int i) {
+  return base + ((i & 1) ? R.sx : 0) + ((i & 2) ? R.sy : 0) + ((i & 4) ? R.sz : 0);
+}
 
-  const int lane = tid & 31, w = tid >> 5;
-  const int px = blockIdx.x * kTileW + (w & 1) * 8 + (lane & 7);
-  const int py = blockIdx.y * kTileH + (w >> 1) * 4 + (lane >> 3);
-  const int W = L.cam.width, H = L.cam.height;
-  const bool active = px < W && py < H;
-  const int ray = py * W + px;
-  const int nrays = W * H;
-  float o[3], d[3], tn = 0.0f;
-  int K = 0, kend = 0;
-  if (active) {
-    ray_setup(L.cam, L.r.lo, L.r.hi, L.r.step, px, py, o, d, tn, K);
-    kend = min(max(L.ck_kend[ray], 0), K);
+__device__ __forceinline__ float corner_weight(const float f[3], int i) {
+  return ((i & 1) ? f[0] : 1.0f - f[0]) * ((i & 2) ? f[1] : 1.0f - f[1]) *
+         ((i & 4) ? f[2] : 1.0f - f[2]);
+}
+
+// Trilinear value from the records' V channel (lerps along x, y, z as in the forward).
+__device__ __forceinline__ float record_value(const RecDev& R, const AdjCell& c, float4 r[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r[i] = __ldg(R.rec + corner_index(R, c.base, i));
+  const float x00 = lerpf(r[0].w, r[1].w, c.f[0]), x10 = lerpf(r[2].w, r[3].w, c.f[0]);
+  const float x01 = lerpf(r[4].w, r[5].w, c.f[0]), x11 = lerpf(r[6].w, r[7].w, c.f[0]);
+  return lerpf(lerpf(x00, x10, c.f[1]), lerpf(x01, x11, c.f[1]), c.f[2]);
+}
+
+__device__ __forceinline__ void flush_tf(float* dst, int i, const float lo[4], const float hi[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (lo[q] != 0.0f) atomicAdd(dst + 4 * i + q, lo[q]);
+    if (hi[q] != 0.0f) atomicAdd(dst + 4 * (i + 1) + q, hi[q]);
   }
-  float4 gr = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (active && kend > 0) gr = __ldg(L.grad_rgba + ray);
+}
+
+// Transmittance before sample kg, recomputed forward from the checkpoint of its
+// 32-sample segment (used when dividing back through a group would lose precision).
+__device__ __noinline__ float recompute_T(const AdjointLaunch& L, const float o[3],
+                                          const float d[3], float tn, int kg, int ray) {
+  const int s0 = (kg >> 5) << 5;
+  float T = s0 == 0 ? 1.0f : L.ck_T[(size_t)((s0 >> 5) - 1) * (L.cam.width * L.cam.height) + ray];
+  for (int j = s0; j < kg; ++j) {
+    const float t = fmaf((float)j + 0.5f, L.r.step, tn);
+    float p[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
+    float4 r[8];
+    const float al = tf_lookup(L.tf, record_value(L.R, adj_cell(L.V, p), r)).rgba.w;
+    if (al != 0.0f) T = T * (1.0f - al);
+  }
+  return T;
+}
+
+
+// Four lanes per ray: lane q takes sample kg + q of every group of four, groups visited from
+// the last to the first.  Per group: the transmittances before each sample come from the
+// transmittance after the group divided by the product of (1 - alpha) over it (exactly
+// re-anchored at every 32-sample checkpoint), and the adjoint of the transmittance follows
+// from a suffix scan of the affine maps Tadj -> alpha g.c + (1 - alpha) Tadj.
+__global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
+  // TF contributions: summed in registers per run of samples that read the same pair of
+  // entries, flushed into a per-warp table in shared memory (tables up to kMaxWarpTf
+  // entries; larger ones go to global memory), which the warp adds to the global result
+  // when it runs out of tiles -- no block-wide barrier.
+  extern __shared__ float smem[];
+  const int tid = threadIdx.x;
+  const bool warp_tf = L.grad_tf && L.tf.n <= kMaxWarpTf;
+  float* tf_dst = warp_tf ? smem + (tid >> 5) * 4 * L.tf.n : L.grad_tf;
+  if (warp_tf)
+    for (int i = (tid & 31); i < 4 * L.tf.n; i += 32) tf_dst[i] = 0.0f;
+  __syncwarp();
+
+  const int lane = tid & 31, q = lane & 3, qd = lane >> 2;
+  const unsigned qmask = 0xFu << (lane & ~3);
+  const int W = L.cam.width, H = L.cam.height;
+  const int nrays = W * H;
+  const int tiles_x = (W + kQuadTileW - 1) / kQuadTileW;
+  const int tiles = tiles_x * ((H + kQuadTileH - 1) / kQuadTileH);
   const float step = L.r.step;
-  float Tadj = -gr.w;
-  const auto* vox = static_cast<const typename VoxelT<VTYPE>::T*>(L.V.data);
-  (void)vox;
-  const int nseg = (kend + kCkptStride - 1) / kCkptStride;
-  for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int k0 = seg * kCkptStride;
-    const int k1 = min(k0 + kCkptStride, kend);
-    float T = seg == 0 ? 1.0f : L.ck_T[(size_t)(seg - 1) * nrays + ray];
-    for (int k = k0; k < k1; ++k) {
-      Ts[(k - k0) * kThreads + tid] = T;
-      const float a = alpha_at<VTYPE>(L.V, L.tf, o, d, tn, step, k);
-      if (a != 0.0f) T = T * (1.0f - a);
+  const float gs = L.r.gscale;
+  for (;;) {
+    int tile = 0;
+    if (lane == 0) tile = (int)atomicAdd(L.tile_counter, 1u);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= tiles) break;
+    const int px = (tile % tiles_x) * kQuadTileW + (qd & 3);
+    const int py = (tile / tiles_x) * kQuadTileH + (qd >> 2);
+    const bool active = px < W && py < H;
+    const int ray = py * W + px;
+    float o[3], d[3], tn = 0.0f;
+    int K = 0, kend = 0;
+    if (active) {
+      ray_setup(L.cam, L.r.lo, L.r.hi, L.r.step, px, py, o, d, tn, K);
+      kend = min(max(L.ck_kend[ray], 0), K);
     }
-    for (int k = k1 - 1; k >= k0; --k) {
-      const float Tk = Ts[(k - k0) * kThreads + tid];
-      const float t = fmaf((float)k + 0.5f, step, tn);
+    float4 gr = make_float4(0.f, 0.f, 0.f, 0.f);
+    float Tcur = 1.0f;
+    if (kend > 0) {
+      gr = __ldg(L.grad_rgba + ray);
+      Tcur = L.ck_Tend[ray];
+    }
+    float Tadj = -gr.w;
+    int tf_run = -1;
+    float tf_lo[4] = {0.f, 0.f, 0.f, 0.f}, tf_hi[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int kg = ((kend - 1) >> 2) << 2; kend > 0 && kg >= 0; kg -= 4) {
+      const int k = kg + q;
+      const bool live = k < kend;
+      float alpha = 0.0f, gc = 0.0f;
       float p[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
-      const Cell c = cell_of(L.V, p);
-      float s, g[3];
-      value_and_gradient<VTYPE, OP>(L.V, c, s, g);
-      const TfSample ts = tf_lookup(L.tf, trilinear<VTYPE>(L.V, c));
-      const float gs = L.r.gscale;
-      const float gh[3] = {g[0] * gs, g[1] * gs, g[2] * gs};
+      AdjCell c;
+      float4 r[8];
+      TfSample ts;
       ShadeOut so;
-      shade(L.r.sh, L.cam, d, p, gh, ts.rgba, so);
-      const float alpha = ts.rgba.w;
-      const float gc = gr.x * so.c[0] + gr.y * so.c[1] + gr.z * so.c[2];
-      const float dalpha = Tk * (gc - Tadj);
-      const float ta = Tk * alpha;
-      const float dc[3] = {ta * gr.x, ta * gr.y, ta * gr.z};
-      Tadj = fmaf(alpha, gc, (1.0f - alpha) * Tadj);
-      // Phong backward: c = rgb (ka + kd diff) + ks spec
-      const float diff = fmaxf(so.nl, 0.0f);
-      const float kk = fmaf(L.r.sh.kd, diff, L.r.sh.ka);
-      float drgba[4] = {dc[0] * kk, dc[1] * kk, dc[2] * kk, dalpha};
-      float dN[3] = {0.f, 0.f, 0.f};
-      if (so.nl > 0.0f) {
-        const float d_diff = L.r.sh.kd * (dc[0] * ts.rgba.x + dc[1] * ts.rgba.y + dc[2] * ts.rgba.z);
+      float gh[3] = {0.f, 0.f, 0.f};
+      if (live) {
+        const float t = fmaf((float)k + 0.5f, step, tn);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) dN[a] = d_diff * so.L[a];
-        if (so.rv > 0.0f && L.r.sh.shininess != 0.0f) {
-          const float d_spec = L.r.sh.ks * (dc[0] + dc[1] + dc[2]);
-          const float dx = d_spec * L.r.sh.shininess * __powf(so.rv, L.r.sh.shininess - 1.0f);
-          const float nv = so.N[0] * so.V[0] + so.N[1] * so.V[1] + so.N[2] * so.V[2];
+        for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
+        c = adj_cell(L.V, p);
+        ts = tf_lookup(L.tf, record_value(L.R, c, r));
+        float g[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-          for (int a = 0; a < 3; ++a) dN[a] += dx * 2.0f * (nv * so.L[a] + so.nl * so.V[a]);
+        for (int i = 0; i < 8; ++i) {
+          const float wci = corner_weight(c.f, i);
+          g[0] = fmaf(wci, r[i].x, g[0]);
+          g[1] = fmaf(wci, r[i].y, g[1]);
+          g[2] = fmaf(wci, r[i].z, g[2]);
         }
-      }
-      // normal backward: N = -g_hat / |g_hat|
-      float dg[3] = {0.f, 0.f, 0.f};
-      if (so.gl * so.gl > 1e-12f && so.gl > 0.0f) {
-        const float il = 1.0f / so.gl;
-        const float nh[3] = {gh[0] * il, gh[1] * il, gh[2] * il};
-        const float dn = dN[0] * nh[0] + dN[1] * nh[1] + dN[2] * nh[2];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) dg[a] = -(dN[a] - dn * nh[a]) * il * gs;  // -> raw units
+        for (int a = 0; a < 3; ++a) gh[a] = g[a] * gs;
+        shade(L.r.sh, L.cam, d, p, gh, ts.rgba, so);
+        alpha = ts.rgba.w;
+        gc = gr.x * so.c[0] + gr.y * so.c[1] + gr.z * so.c[2];
       }
-      // transfer-function backward
-      float ds = 0.0f;
-      if (L.grad_tf || L.adj) {
-        const int i = ts.i;
-        const float wt = ts.w;
-        if (ts.inside) {
-          const float4 ta4 = __ldg(L.tf.tf + i), tb4 = __ldg(L.tf.tf + i + 1);
-          ds = (drgba[0] * (tb4.x - ta4.x) + drgba[1] * (tb4.y - ta4.y) +
-                drgba[2] * (tb4.z - ta4.z) + drgba[3] * (tb4.w - ta4.w)) * L.tf.scale;
+      // transmittances: exclusive / inclusive prefix products of (1 - alpha) over the group
+      const float om = 1.0f - alpha;
+      float P = om;
+      float u = __shfl_up_sync(qmask, P, 1, 4);
+      if (q >= 1) P *= u;
+      u = __shfl_up_sync(qmask, P, 2, 4);
+      if (q >= 2) P *= u;
+      float E = __shfl_up_sync(qmask, P, 1, 4);
+      if (q == 0) E = 1.0f;
+      const float prod = __shfl_sync(qmask, P, 3, 4);
+      float Tb;
+      if (kg == 0) Tb = 1.0f;
+      else if ((kg & (kCkptStride - 1)) == 0) Tb = L.ck_T[(size_t)((kg >> 5) - 1) * nrays + ray];
+      else if (prod > 1e-4f) Tb = Tcur / prod;
+      else Tb = recompute_T(L, o, d, tn, kg, ray);
+      const float Tk = Tb * E;
+      // adjoint of T: suffix scan of x -> A + B x over the group
+      float A = alpha * gc, B = om;
+      float An = __shfl_down_sync(qmask, A, 1, 4), Bn = __shfl_down_sync(qmask, B, 1, 4);
+      if (q <= 2) {
+        A = fmaf(B, An, A);
+        B = B * Bn;
+      }
+      An = __shfl_down_sync(qmask, A, 2, 4);
+      Bn = __shfl_down_sync(qmask, B, 2, 4);
+      if (q <= 1) {
+        A = fmaf(B, An, A);
+        B = B * Bn;
+      }
+      float Ae = __shfl_down_sync(qmask, A, 1, 4), Be = __shfl_down_sync(qmask, B, 1, 4);
+      if (q == 3) {
+        Ae = 0.0f;
+        Be = 1.0f;
+      }
+      const float Tadj_next = fmaf(Be, Tadj, Ae);  // adjoint of T after this lane's sample
+      const float A0 = __shfl_sync(qmask, A, 0, 4), B0 = __shfl_sync(qmask, B, 0, 4);
+      if (live) {
+        const float dalpha = Tk * (gc - Tadj_next);
+        const float ta = Tk * alpha;
+        const float dc[3] = {ta * gr.x, ta * gr.y, ta * gr.z};
+        // Phong backward: c = rgb (ka + kd diff) + ks spec
+        const float diff = fmaxf(so.nl, 0.0f);
+        const float kk = fmaf(L.r.sh.kd, diff, L.r.sh.ka);
+        float drgba[4] = {dc[0] * kk, dc[1] * kk, dc[2] * kk, dalpha};
+        float dN[3] = {0.f, 0.f, 0.f};
+        if (so.nl > 0.0f) {
+          const float d_diff = L.r.sh.kd * (dc[0] * ts.rgba.x + dc[1] * ts.rgba.y + dc[2] * ts.rgba.z);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) dN[a] = d_diff * so.L[a];
+          if (so.rv > 0.0f && L.r.sh.shininess != 0.0f) {
+            const float d_spec = L.r.sh.ks * (dc[0] + dc[1] + dc[2]);
+            const float dx = d_spec * L.r.sh.shininess * __powf(so.rv, L.r.sh.shininess - 1.0f);
+            const float nv = so.N[0] * so.V[0] + so.N[1] * so.V[1] + so.N[2] * so.V[2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dN[a] += dx * 2.0f * (nv * so.L[a] + so.nl * so.V[a]);
+          }
         }
-        if (L.grad_tf) {
-          float* dst = shared_tf ? hist : L.grad_tf;
+        // normal backward: N = -g_hat / |g_hat|, then to the unscaled operator gradient
+        float dg[3] = {0.f, 0.f, 0.f};
+        if (so.gl * so.gl > 1e-12f && so.gl > 0.0f) {
+          const float il = 1.0f / so.gl;
+          const float nh[3] = {gh[0] * il, gh[1] * il, gh[2] * il};
+          const float dn = dN[0] * nh[0] + dN[1] * nh[1] + dN[2] * nh[2];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float v0 = (1.0f - wt) * drgba[q], v1 = wt * drgba[q];
-            if (v0 != 0.0f) atomicAdd(dst + 4 * i + q, v0);
-            if (v1 != 0.0f) atomicAdd(dst + 4 * (i + 1) + q, v1);
+          for (int a = 0; a < 3; ++a) dg[a] = -(dN[a] - dn * nh[a]) * il * gs;
+        }
+        // transfer-function backward
+        float ds = 0.0f;
+        {
+          const int i = ts.i;
+          const float wt = ts.w;
+          if (ts.inside) {
+            const float4 ta4 = __ldg(L.tf.tf + i), tb4 = __ldg(L.tf.tf + i + 1);
+            ds = (drgba[0] * (tb4.x - ta4.x) + drgba[1] * (tb4.y - ta4.y) +
+                  drgba[2] * (tb4.z - ta4.z) + drgba[3] * (tb4.w - ta4.w)) * L.tf.scale;
+          }
+          if (L.grad_tf) {
+            if (i != tf_run) {
+              if (tf_run >= 0) flush_tf(tf_dst, tf_run, tf_lo, tf_hi);
+              tf_run = i;
+#pragma unroll
+              for (int j = 0; j < 4; ++j) tf_lo[j] = tf_hi[j] = 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              tf_lo[j] = fmaf(1.0f - wt, drgba[j], tf_lo[j]);
+              tf_hi[j] = fmaf(wt, drgba[j], tf_hi[j]);
+            }
+          }
+        }
+        // scatter (dL/dV direct, dL/dG) to the cell corners
+        if (L.adj && (ds != 0.0f || dg[0] != 0.0f || dg[1] != 0.0f || dg[2] != 0.0f)) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float wci = corner_weight(c.f, i);
+            atomicAdd(L.adj + corner_index(L.R, c.base, i),
+                      make_float4(wci * ds, wci * dg[0], wci * dg[1], wci * dg[2]));
           }
         }
       }
-      // scatter (dL/ds, dL/dG) to the cell corners
-      if (L.adj && (ds != 0.0f || dg[0] != 0.0f || dg[1] != 0.0f || dg[2] != 0.0f)) {
-        const int nx = L.V.n[0], ny = L.V.n[1], nz = L.V.n[2];
-#pragma unroll
-        for (int cc = 0; cc < 8; ++cc) {
-          const float wx = (cc & 1) ? c.f[0] : 1.0f - c.f[0];
-          const float wy = (cc & 2) ? c.f[1] : 1.0f - c.f[1];
-          const float wz = (cc & 4) ? c.f[2] : 1.0f - c.f[2];
-          const float wc = wx * wy * wz;
-          const int x = min(c.ib[0] + (cc & 1), nx - 1);
-          const int y = min(c.ib[1] + ((cc >> 1) & 1), ny - 1);
-          const int z = min(c.ib[2] + ((cc >> 2) & 1), nz - 1);
-          atomicAdd(L.adj + ((size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)),
-                    make_float4(wc * ds, wc * dg[0], wc * dg[1], wc * dg[2]));
-        }
-      }
+      Tcur = Tb;
+      Tadj = fmaf(B0, Tadj, A0);
     }
+    if (L.grad_tf && tf_run >= 0) flush_tf(tf_dst, tf_run, tf_lo, tf_hi);
+    __syncwarp();
   }
-  if (shared_tf) {
-    __syncthreads();
-    for (int i = tid; i < 4 * L.tf.n; i += kThreads) {
-      const float v = hist[i];
+  if (warp_tf) {
+    __syncwarp();
+    for (int i = (tid & 31); i < 4 * L.tf.n; i += 32) {
+      const float v = tf_dst[i];
       if (v != 0.0f) atomicAdd(L.grad_tf + i, v);
     }
   }
 }
 
-template <int VTYPE, int OP>
-static void launch_adj_typed(const AdjointLaunch& L, dim3 grid, size_t smem, cudaStream_t s) {
-  k_adjoint<VTYPE, OP><<<grid, kThreads, smem, s>>>(L);
-}
-
-template <int VTYPE>
-static void launch_adj_op(const AdjointLaunch& L, dim3 grid, size_t smem, cudaStream_t s) {
-  switch (L.op) {
-    case OP_CENTRAL: launch_adj_typed<VTYPE, OP_CENTRAL>(L, grid, smem, s); break;
-    case OP_SOBEL: launch_adj_typed<VTYPE, OP_SOBEL>(L, grid, smem, s); break;
-    default: launch_adj_typed<VTYPE, OP_ZH>(L, grid, smem, s);
-  }
+static int adjoint_blocks(size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint, kThreads, smem);
+  return (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
 }
 
 cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t s) {
-  const dim3 grid((L.cam.width + kTileW - 1) / kTileW, (L.cam.height + kTileH - 1) / kTileH);
-  size_t smem = sizeof(float) * kCkptStride * kThreads;
-  if (L.grad_tf && L.tf.n <= kMaxSharedTf) smem += sizeof(float) * 4 * L.tf.n;
-  switch (L.dtype) {
-    case VT_U8: launch_adj_op<VT_U8>(L, grid, smem, s); break;
-    case VT_U16: launch_adj_op<VT_U16>(L, grid, smem, s); break;
-    case VT_F16: launch_adj_op<VT_F16>(L, grid, smem, s); break;
-    default: launch_adj_op<VT_F32>(L, grid, smem, s);
-  }
+  const size_t smem = (L.grad_tf && L.tf.n <= kMaxWarpTf) ? sizeof(float) * 4 * L.tf.n * (kThreads / 32) : 0;
+  cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  k_adjoint<<<adjoint_blocks(smem), kThreads, smem, s>>>(L);
   return cudaGetLastError();
 }
 

@@ -248,7 +248,8 @@ RecDev rec_dev(const vr_ctx* ctx) {
 }
 
 static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* out,
-                               int* ck_kend, float* ck_T, int nslots, cudaStream_t s) {
+                               int* ck_kend, float* ck_T, int nslots, cudaStream_t s,
+                               float* ck_Tend = nullptr) {
   vr_status rst = ensure_records(ctx, p, s);
   if (rst != VR_OK) return rst;
   MarchLaunch L;
@@ -264,6 +265,7 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
   L.tile_counter = reinterpret_cast<unsigned*>(ctx->stats + 4);
   L.ck_kend = ck_kend;
   L.ck_T = ck_T;
+  L.ck_Tend = ck_Tend;
   L.nslots = nslots;
   if (p->collect_stats) {
     vr_status st = cuda_status(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
@@ -282,7 +284,8 @@ static void ckpt_layout(vr_ctx* ctx, const vr_render_params* p, int* nrays, int*
   *nrays = ctx->cam.width * ctx->cam.height;
   const int kmax = max_samples(ctx, p);
   *nslots = kmax > 1 ? (kmax - 1) / kCkptStride : 0;
-  *bytes = align256((size_t)*nrays * 4) + (size_t)*nrays * 4 * (size_t)*nslots;
+  // per ray: end index, final transmittance, transmittance before every 32nd sample
+  *bytes = 2 * align256((size_t)*nrays * 4) + (size_t)*nrays * 4 * (size_t)*nslots;
 }
 
 }  // namespace vr
@@ -502,8 +505,10 @@ vr_status vr_render_forward_train(vr_ctx* ctx, const vr_render_params* params, f
   if (!is_device_pointer(out_rgba) || !is_device_pointer(checkpoints)) return VR_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* kend = static_cast<int*>(checkpoints);
-  float* T = reinterpret_cast<float*>(static_cast<char*>(checkpoints) + align256((size_t)nrays * 4));
-  st = render_common(ctx, params, out_rgba, kend, T, nslots, s);
+  float* Tend = reinterpret_cast<float*>(static_cast<char*>(checkpoints) + align256((size_t)nrays * 4));
+  float* T = reinterpret_cast<float*>(static_cast<char*>(checkpoints) +
+                                      2 * align256((size_t)nrays * 4));
+  st = render_common(ctx, params, out_rgba, kend, T, nslots, s, Tend);
   if (st != VR_OK) return st;
   // remember what was recorded (replace an older record of the same buffer)
   int slot = -1;
@@ -525,55 +530,90 @@ vr_status vr_render_forward_train(vr_ctx* ctx, const vr_render_params* params, f
   return VR_OK;
 }
 
-vr_status vr_render_backward(vr_ctx* ctx, const vr_render_params* params, const void* checkpoints,
-                             const float* grad_rgba, float* grad_volume, float* grad_tf,
-                             void* stream) {
-  if (!ctx || !checkpoints || !grad_rgba) return VR_ERR_INVALID_ARG;
+vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, int nviews,
+                                   const vr_camera* cams, const void* const* checkpoints,
+                                   const float* const* grad_rgba, float* grad_volume,
+                                   float* grad_tf, void* stream) {
+  if (!ctx || nviews < 1 || !cams || !checkpoints || !grad_rgba) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
-  if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
-  const CkptRecord* rec = nullptr;
-  for (int i = 0; i < kMaxCkptRecords; ++i)
-    if (ctx->ckpt[i].ptr == checkpoints) rec = &ctx->ckpt[i];
-  if (!rec) return VR_ERR_STATE;
-  if (rec->vol_gen != ctx->vol_gen || rec->tf_gen != ctx->tf_gen) return VR_ERR_STATE;
-  if (std::memcmp(&rec->cam, &ctx->cam, sizeof(vr_camera)) != 0) return VR_ERR_STATE;
-  vr_render_params a = rec->params, b = *params;
-  a.collect_stats = b.collect_stats = 0;
-  if (std::memcmp(&a, &b, sizeof(vr_render_params)) != 0) return VR_ERR_STATE;
+  if (!ctx->has_volume || !ctx->has_tf) return VR_ERR_STATE;
+  // validate every view before queuing any work
+  const CkptRecord* recs[256];
+  if (nviews > 256) return VR_ERR_INVALID_ARG;
+  for (int v = 0; v < nviews; ++v) {
+    if (!checkpoints[v] || !grad_rgba[v]) return VR_ERR_INVALID_ARG;
+    const CkptRecord* rec = nullptr;
+    for (int i = 0; i < kMaxCkptRecords; ++i)
+      if (ctx->ckpt[i].ptr == checkpoints[v]) rec = &ctx->ckpt[i];
+    if (!rec) return VR_ERR_STATE;
+    if (rec->vol_gen != ctx->vol_gen || rec->tf_gen != ctx->tf_gen) return VR_ERR_STATE;
+    if (std::memcmp(&rec->cam, &cams[v], sizeof(vr_camera)) != 0) return VR_ERR_STATE;
+    vr_render_params a = rec->params, b = *params;
+    a.collect_stats = b.collect_stats = 0;
+    if (std::memcmp(&a, &b, sizeof(vr_render_params)) != 0) return VR_ERR_STATE;
+    recs[v] = rec;
+  }
   DeviceGuard g(ctx->device);
   if (!g.ok) return cuda_status(cudaGetLastError());
-  if (!is_device_pointer(grad_rgba)) return VR_ERR_INVALID_ARG;
+  for (int v = 0; v < nviews; ++v)
+    if (!is_device_pointer(grad_rgba[v])) return VR_ERR_INVALID_ARG;
   if (grad_volume && !is_device_pointer(grad_volume)) return VR_ERR_INVALID_ARG;
   if (grad_tf && !is_device_pointer(grad_tf)) return VR_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t nvox = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
-  void* adj = ctx->adj;
-  st = ensure(ctx, &adj, &ctx->adj_cap, nvox * sizeof(float4));
+  if (grad_volume) {
+    void* adj = ctx->adj;
+    st = ensure(ctx, &adj, &ctx->adj_cap, nvox * sizeof(float4));
+    if (st != VR_OK) return st;
+    ctx->adj = static_cast<float4*>(adj);
+    st = cuda_status(cudaMemsetAsync(ctx->adj, 0, nvox * sizeof(float4), s));
+    if (st != VR_OK) return st;
+  }
+  // the adjoint visits every sample (no skipping): records are needed everywhere
+  vr_render_params all = *params;
+  all.skip_empty = 0;
+  st = ensure_records(ctx, &all, s);
   if (st != VR_OK) return st;
-  ctx->adj = static_cast<float4*>(adj);
-  st = cuda_status(cudaMemsetAsync(ctx->adj, 0, nvox * sizeof(float4), s));
-  if (st != VR_OK) return st;
-  AdjointLaunch L;
-  L.V = vol_dev(ctx);
-  L.tf = tf_dev(ctx);
-  L.cam = ctx->camdev;
-  L.r = render_dev(ctx, params);
-  L.dtype = (int)ctx->dtype;
-  L.op = params->grad;
-  L.ck_kend = static_cast<const int*>(checkpoints);
-  L.ck_T = reinterpret_cast<const float*>(static_cast<const char*>(checkpoints) +
-                                          align256((size_t)rec->nrays * 4));
-  L.nslots = rec->nslots;
-  L.grad_rgba = reinterpret_cast<const float4*>(grad_rgba);
-  L.adj = grad_volume ? ctx->adj : nullptr;
-  L.grad_tf = grad_tf;
-  st = cuda_status(launch_adjoint(L, s));
-  if (st != VR_OK) return st;
+  for (int v = 0; v < nviews; ++v) {
+    const CkptRecord* rec = recs[v];
+    CamDev basis;
+    st = check_camera(&cams[v], &basis);
+    if (st != VR_OK) return st;
+    AdjointLaunch L;
+    L.V = vol_dev(ctx);
+    L.R = rec_dev(ctx);
+    L.tf = tf_dev(ctx);
+    L.cam = basis;
+    L.r = render_dev(ctx, params);
+    L.dtype = (int)ctx->dtype;
+    L.op = params->grad;
+    L.ck_kend = static_cast<const int*>(checkpoints[v]);
+    L.ck_Tend = reinterpret_cast<const float*>(static_cast<const char*>(checkpoints[v]) +
+                                               align256((size_t)rec->nrays * 4));
+    L.ck_T = reinterpret_cast<const float*>(static_cast<const char*>(checkpoints[v]) +
+                                            2 * align256((size_t)rec->nrays * 4));
+    L.tile_counter = reinterpret_cast<unsigned*>(ctx->stats + 5);
+    L.nslots = rec->nslots;
+    L.grad_rgba = reinterpret_cast<const float4*>(grad_rgba[v]);
+    L.adj = grad_volume ? ctx->adj : nullptr;
+    L.grad_tf = grad_tf;
+    st = cuda_status(launch_adjoint(L, s));
+    if (st != VR_OK) return st;
+  }
   if (grad_volume)
     st = cuda_status(launch_adjoint_volume(ctx->adj, ctx->n, params->grad, 1.0f / ctx->value_max,
                                            grad_volume, s));
   return st;
+}
+
+vr_status vr_render_backward(vr_ctx* ctx, const vr_render_params* params, const void* checkpoints,
+                             const float* grad_rgba, float* grad_volume, float* grad_tf,
+                             void* stream) {
+  if (!ctx || !checkpoints || !grad_rgba) return VR_ERR_INVALID_ARG;
+  if (!ctx->has_camera) return VR_ERR_STATE;
+  return vr_render_backward_views(ctx, params, 1, &ctx->cam, &checkpoints, &grad_rgba,
+                                  grad_volume, grad_tf, stream);
 }
 
 vr_status vr_read_stats(vr_ctx* ctx, vr_stats* out, void* stream) {

@@ -125,19 +125,23 @@ struct MarchLaunch {
   unsigned long long* stats;  // NULL: no counting
   unsigned* tile_counter;     // work counter of the persistent launch (zeroed per launch)
   int* ck_kend;               // NULL: no checkpoints
-  float* ck_T;
+  float* ck_T;                // transmittance before every 32nd sample, [slot][ray]
+  float* ck_Tend;             // transmittance after the last sample, [ray]
   int nslots;
 };
 cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s);
 
 struct AdjointLaunch {
   VolDev V;
+  RecDev R;
   TfDev tf;
   CamDev cam;
   RenderDev r;
   int dtype, op;
   const int* ck_kend;
   const float* ck_T;
+  const float* ck_Tend;
+  unsigned* tile_counter;  // work counter of the persistent launch (zeroed per launch)
   int nslots;
   const float4* grad_rgba;
   float4* adj;     // per voxel corner accumulators (dL/ds, dL/dG) over the unpadded grid

@@ -164,7 +164,10 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
   const int kend = k < K ? k : K;
   if (active && q == 0) {
     reinterpret_cast<float4*>(L.out)[ray] = make_float4(C0, C1, C2, 1.0f - T);
-    if (CKPT) L.ck_kend[ray] = kend;
+    if (CKPT) {
+      L.ck_kend[ray] = kend;
+      L.ck_Tend[ray] = T;
+    }
     hit += K > 0 ? 1u : 0u;
     plain += (unsigned)kend;
   }

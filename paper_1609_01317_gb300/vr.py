@@ -65,6 +65,10 @@ _SIGS = [
     ("vr_render_backward", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("vr_read_stats", C.c_int, [C.c_void_p, C.POINTER(vr_stats), C.c_void_p]),
+    ("vr_render_backward_views", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_int,
+                                           C.POINTER(vr_camera), C.POINTER(C.c_void_p),
+                                           C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p,
+                                           C.c_void_p]),
     ("vr_render_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                                     C.c_void_p, C.c_int, C.POINTER(vr_camera),
                                     C.POINTER(vr_render_params), C.c_void_p, C.c_void_p]),
@@ -189,6 +193,17 @@ def vr_render_noalloc(voxels, dtype, nx, ny, nz, value_max, tf_rgba, ntf, cam, p
            lib().vr_render_noalloc(_ptr(voxels), dt, int(nx), int(ny), int(nz), float(value_max),
                                    _ptr(tf_rgba), int(ntf), C.byref(c), C.byref(params),
                                    _ptr(out_rgba), stream))
+
+
+def vr_render_backward_views(ctx, params, cams, checkpoints, grad_rgbas, grad_volume, grad_tf,
+                             stream=None):
+    n = len(cams)
+    carr = (vr_camera * n)(*[c if isinstance(c, vr_camera) else make_camera(c) for c in cams])
+    karr = (C.c_void_p * n)(*[_ptr(k) for k in checkpoints])
+    garr = (C.c_void_p * n)(*[_ptr(g) for g in grad_rgbas])
+    _check("vr_render_backward_views",
+           lib().vr_render_backward_views(ctx, C.byref(params), n, carr, karr, garr,
+                                          _ptr(grad_volume), _ptr(grad_tf), stream))
 
 
 def vr_read_stats(ctx, stream=None) -> dict:

@@ -283,3 +283,40 @@ def test_autograd_multi_view_training_reduces_loss(R):
         losses.append(float(loss))
     assert all(math.isfinite(l) for l in losses)
     assert losses[-1] < 0.8 * losses[0], losses
+
+
+def test_multi_view_backward_equals_sum_of_single_views(R):
+    import torch
+    from paper_1609_01317_gb300 import vr
+
+    n = 24
+    vol = torch.from_numpy(P.blurred_random_field(7, n)).cuda()
+    tf = torch.from_numpy(P.tf_c1(64)).cuda()
+    views = P.training_views(n, 32, 32)[::3]
+    params = vr.make_params(grad="zucker_hummel", skip_empty=False)
+    R.upload_volume(vol, 1.0, "f32")
+    R.set_transfer_function(tf)
+    cks, grads = [], []
+    rng = torch.Generator(device="cuda").manual_seed(5)
+    for cam in views:
+        R.set_camera(cam)
+        nb = vr.vr_checkpoint_bytes(R.ctx, params)
+        ck = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+        ckv = ck[(-ck.data_ptr()) % 256:][:nb]
+        img = torch.empty((32, 32, 4), device="cuda")
+        vr.vr_render_forward_train(R.ctx, params, img, ckv, nb)
+        cks.append((ck, ckv))
+        grads.append(torch.randn((32, 32, 4), device="cuda", generator=rng))
+    gv1, gt1 = torch.zeros_like(vol), torch.zeros_like(tf)
+    for cam, (_, ckv), g in zip(views, cks, grads):
+        R.set_camera(cam)
+        vr.vr_render_backward(R.ctx, params, ckv, g, gv1, gt1)
+    gv2, gt2 = torch.zeros_like(vol), torch.zeros_like(tf)
+    vr.vr_render_backward_views(R.ctx, params, views, [c[1] for c in cks], grads, gv2, gt2)
+    torch.cuda.synchronize()
+    assert gv1.abs().max() > 0 and gt1.abs().max() > 0
+    torch.testing.assert_close(gv2, gv1, rtol=1e-4, atol=1e-5 * float(gv1.abs().max()))
+    torch.testing.assert_close(gt2, gt1, rtol=1e-4, atol=1e-5 * float(gt1.abs().max()))
+    # a camera that does not match the recorded checkpoints is refused
+    with pytest.raises(vr.VrError):
+        vr.vr_render_backward_views(R.ctx, params, views[::-1], [c[1] for c in cks], grads, gv2, gt2)
