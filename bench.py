@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", choices=["ct", "ellipsoids", "sphere"], default="ct")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="edge scale of the batched-render volumes (1.0 = full sizes)")
     return ap.parse_args()
 
 
@@ -179,7 +181,9 @@ def sum_over_ranks(x, world):
 
 # ------------------------------------------------------------------ CPU oracle leg
 def oracle_sample(w, seconds):
-    """Time the FP64 oracle on a band of image rows (bounded to about `seconds`)."""
+    """Time the FP64 oracle on the workload's frame: whole frames (rows split over the
+    host cores) until about `seconds` have passed (at least one frame, at most four), or a
+    band of rows around the middle when one frame alone would take far longer."""
     import oracle
 
     ov = oracle.OracleVolume(w["volume"], w["value_max"])
@@ -187,17 +191,28 @@ def oracle_sample(w, seconds):
     cam = w["camera"]
     H = cam["height"]
     mid = H // 2
-    rows = 2
     t0 = time.perf_counter()
-    _, _, total = oracle.render(ov, w["tf"], cam, pr, rows=(mid, mid + rows))
+    _, _, probe = oracle.render(ov, w["tf"], cam, pr, rows=(mid - 4, mid + 4))
     dt = time.perf_counter() - t0
-    # grow the band so that the measured run lasts about `seconds`
-    target = max(2, min(H // 2, int(rows * seconds / max(dt, 1e-3))))
-    r0 = max(0, mid - target // 2)
+    est_frame = dt * H / 8.0 * 0.6  # the middle band is denser than the frame average
+    if est_frame > 3.0 * seconds:
+        rows = max(8, int(8 * seconds / max(dt, 1e-3)))
+        r0 = max(0, mid - rows // 2)
+        t0 = time.perf_counter()
+        _, _, total = oracle.render(ov, w["tf"], cam, pr, rows=(r0, min(H, r0 + rows)))
+        dt = time.perf_counter() - t0
+        return {"samples": int(total), "seconds": dt, "rows": [r0, min(H, r0 + rows)],
+                "frames": 0, "cores": oracle.num_threads()}
+    total, frames = 0, 0
     t0 = time.perf_counter()
-    _, _, total = oracle.render(ov, w["tf"], cam, pr, rows=(r0, r0 + target))
+    while frames < 4:
+        _, _, n = oracle.render(ov, w["tf"], cam, pr)
+        total += n
+        frames += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
     dt = time.perf_counter() - t0
-    return {"samples": int(total), "seconds": dt, "rows": [r0, r0 + target],
+    return {"samples": int(total), "seconds": dt, "rows": [0, H], "frames": frames,
             "cores": oracle.num_threads()}
 
 
@@ -209,7 +224,7 @@ def run_reference(args):
     vals = []
     samples = 0
     secs = 0.0
-    per_step = max(3.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
         r = oracle_sample(w, per_step)
         if i >= args.warmup:
@@ -227,8 +242,9 @@ def run_reference(args):
                    "grad": w["grad"], "step": w["step"]},
         "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": r["cores"],
                          "kind": "oracle",
-                         "sample": f"rows {r['rows'][0]}-{r['rows'][1]} of the "
-                                   f"{cam['width']}x{cam['height']} frame per step"},
+                         "sample": (f"{r['frames']} whole frame(s)" if r["frames"] else
+                                    f"rows {r['rows'][0]}-{r['rows'][1]}") +
+                                   f" of the {cam['width']}x{cam['height']} frame per step"},
         "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -237,6 +253,74 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------ GPU leg
+def batch_leg(args):
+    """Batched workload: 8 volumes (96^3 .. 384x384x256, uint8/uint16), 64 orbit cameras
+    each at 512x512, central differences, skipping on.  One graph-replayed persistent launch
+    (after the autotuner) against 512 separate vr_render calls."""
+    import torch
+
+    import phantoms as P
+    from paper_1609_01317_gb300 import Renderer, vr
+
+    t0 = time.perf_counter()
+    wl = P.workload_batch(args.batch_scale)
+    gen_s = time.perf_counter() - t0
+    params = vr.make_params(grad="central", skip_empty=True)
+    pst = vr.make_params(grad="central", skip_empty=True, collect_stats=True)
+    rends, cams, owner = [], [], []
+    for i, w in enumerate(wl):
+        r = Renderer(torch.cuda.current_device())
+        r.upload_volume(w["volume"], w["value_max"])
+        r.set_transfer_function(w["tf"])
+        rends.append(r)
+        cams += w["cameras"]
+        owner += [i] * len(w["cameras"])
+    outs = [torch.empty((c["height"], c["width"], 4), device="cuda") for c in cams]
+    cam_s = [vr.make_camera(c) for c in cams]
+    samples = 0
+    for c, o, out in zip(cam_s, owner, outs):
+        vr.vr_set_camera(rends[o].ctx, c)
+        vr.vr_render(rends[o].ctx, pst, out)
+        samples += vr.vr_read_stats(rends[o].ctx)["samples_plain"]
+    b = vr.vr_batch_create([r.ctx for r in rends], cams, owner, params, outs)
+    chosen = vr.vr_batch_autotune(b)
+    sh = torch.cuda.current_stream().cuda_stream or None
+
+    def batched():
+        vr.vr_batch_run(b, sh)
+
+    def separate():
+        for c, o, out in zip(cam_s, owner, outs):
+            vr.vr_set_camera(rends[o].ctx, c)
+            vr.vr_render(rends[o].ctx, params, out, sh)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, min(args.steps, 5))
+    t_b = timed(batched, reps)
+    t_s = timed(separate, reps)
+    vr.vr_batch_destroy(b)
+    for r in rends:
+        r.close()
+    n = len(cams)
+    return {"workload": f"batch8vol_{n}renders_512_cd", "renders": n, "samples": samples,
+            "volume_scale": args.batch_scale, "autotuned": {"threads": chosen[0],
+                                                            "tile": [chosen[1], chosen[2]]},
+            "batched_ms": t_b, "separate_ms": t_s, "speedup": t_s / t_b,
+            "batched_gsamples_s": samples / (t_b / 1e3) / 1e9,
+            "separate_gsamples_s": samples / (t_s / 1e3) / 1e9,
+            "renders_per_s": n / (t_b / 1e3), "phantom_generation_s": gen_s}
+
+
 def fwd_bwd_leg(R, args):
     """Differentiable workload: 128^3 float32 blurred density, learnable 256-entry TF,
     16 views at 256x256, central differences, step 0.5.  Times the forward that records
@@ -423,6 +507,7 @@ def run_ours(args):
 
     if not args.no_extras:
         line["fwd_bwd"] = fwd_bwd_leg(R, args)
+        line["batch"] = batch_leg(args)
     if not args.no_extras and world == 1:
         # end to end through the C ABI with host buffers: H2D of the volume and TF, D2H of
         # the image, every step
@@ -451,9 +536,11 @@ def run_ours(args):
                        "matches_device_result": bool(ok)}
         # CPU baseline: the FP64 oracle on a bounded sample of the same workload
         cb = oracle_sample(w, args.cpu_seconds)
+        what = (f"{cb['frames']} whole frame(s)" if cb["frames"] else
+                f"image rows {cb['rows'][0]}-{cb['rows'][1]}")
         line["cpu_baseline"] = {"value": cb["samples"] / cb["seconds"] / 1e9,
                                 "unit": "Gsamples/s", "cores": cb["cores"], "kind": "oracle",
-                                "sample": f"image rows {cb['rows'][0]}-{cb['rows'][1]} "
+                                "sample": f"{what} of the workload "
                                           f"({cb['samples']} samples, {cb['seconds']:.1f} s)"}
     else:
         line["e2e"] = None

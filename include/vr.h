@@ -212,6 +212,33 @@ vr_status vr_render_backward_views(vr_ctx *ctx, const vr_render_params *params, 
  * `stream`.  Errors: INVALID_ARG, STATE (no such render), CUDA. */
 vr_status vr_read_stats(vr_ctx *ctx, vr_stats *out, void *stream);
 
+/* ---- Batched rendering -------------------------------------------------------------
+ * Many renders -- ncams cameras, camera i over the volume of ctxs[ctx_of_cam[i]] -- in one
+ * persistent launch (rays are independent, §2.2), captured once into a CUDA graph and
+ * replayed by vr_batch_run.  Every context must hold a volume and a transfer function;
+ * volumes may differ in size and voxel type.  outs[i] is camera i's H x W x 4 float32
+ * device image (caller-owned, must outlive the batch).  The batch records the contexts'
+ * state at creation: vr_batch_run returns VR_ERR_STATE once any of them has a new volume
+ * or transfer function (create a new batch then).  Device tables are allocated with
+ * ctxs[0]'s allocator; destroy the batch before its contexts.  collect_stats must be 0.
+ * Errors: INVALID_ARG, STATE, UNSUPPORTED (contexts on different devices, stats),
+ * OUT_OF_MEMORY, CUDA. */
+typedef struct vr_batch vr_batch;
+vr_status vr_batch_create(vr_batch **out, vr_ctx *const *ctxs, int nctx, const vr_camera *cams,
+                          const int *ctx_of_cam, int ncams, const vr_render_params *params,
+                          float *const *outs, void *stream);
+
+/* Replay the batch's graph on `stream` (asynchronous). */
+vr_status vr_batch_run(vr_batch *batch, void *stream);
+
+/* Time the batch with each block size (64, 128, 256 threads) and warp tile shape (4x2,
+ * 2x4, 8x1 rays) on `stream` (synchronising), keep the fastest and rebuild the graph.
+ * chosen (optional, 3 ints) receives {threads, tile width, tile height}. */
+vr_status vr_batch_autotune(vr_batch *batch, void *stream, int *chosen);
+
+/* Release the batch (synchronises the device).  NULL is a no-op. */
+void vr_batch_destroy(vr_batch *batch);
+
 /* Short English text of a status code (static storage). */
 const char *vr_status_string(vr_status status);
 

@@ -213,7 +213,7 @@ static vr_status refresh_visibility(vr_ctx* ctx, cudaStream_t s) {
 
 // Operator gradient records for the current volume, operator and (with skipping) the
 // current brick visibility; recomputed only when one of them changed.
-static vr_status ensure_records(vr_ctx* ctx, const vr_render_params* p, cudaStream_t s) {
+vr_status ensure_records(vr_ctx* ctx, const vr_render_params* p, cudaStream_t s) {
   const bool skip = p->skip_empty != 0;
   if (ctx->rec_valid && ctx->rec_vol_gen == ctx->vol_gen && ctx->rec_op == p->grad &&
       (ctx->rec_all || (skip && ctx->rec_tf_gen == ctx->tf_gen)))

@@ -99,6 +99,9 @@ bool is_device_pointer(const void* p);
 // device descriptors
 VolDev vol_dev(const vr_ctx* ctx);
 RenderDev render_dev_for(const int n[3], float value_max, const vr_render_params* p);
+RecDev rec_dev(const vr_ctx* ctx);
+// gradient records of the context's volume for `p` (recomputed on `s` when stale)
+vr_status ensure_records(vr_ctx* ctx, const vr_render_params* p, cudaStream_t s);
 TfDev tf_dev(const vr_ctx* ctx);
 RenderDev render_dev(const vr_ctx* ctx, const vr_render_params* p);
 int max_samples(const vr_ctx* ctx, const vr_render_params* p);

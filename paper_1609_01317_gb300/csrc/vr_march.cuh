@@ -1,0 +1,168 @@
+// vr_march.cuh -- the per-ray march shared by the single-frame and batched kernels.
+//
+// Four lanes (a quad) march one ray: lane q evaluates sample k + q of every group of four
+// consecutive samples and every lane composites the group in sample order (§3.9, Eq. 6).
+// The sample's value and operator gradient come from the 8 gradient records of its cell
+// (§3.4, §3.5), then the transfer function (§3.7) and Phong (§3.8).
+#pragma once
+
+#include "vr_internal.h"
+
+namespace vr {
+
+// Corner records of cell c and the trilinear value (raw units), lerps along x, y, z.
+struct Corners {
+  float4 r[8];  // index bit 0: +x, bit 1: +y, bit 2: +z
+};
+
+__device__ __forceinline__ void corners_load(const RecDev& R, const Cell& c, Corners& k) {
+  const size_t base = (size_t)c.ib[0] + (size_t)R.n[0] * ((size_t)c.ib[1] + (size_t)R.n[1] * c.ib[2]);
+  const float4* __restrict__ p = R.rec + base;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    k.r[i] = __ldg(p + ((i & 1) ? R.sx : 0) + ((i & 2) ? R.sy : 0) + ((i & 4) ? R.sz : 0));
+}
+
+__device__ __forceinline__ float corners_value(const Corners& k, const Cell& c) {
+  const float x00 = lerpf(k.r[0].w, k.r[1].w, c.f[0]), x10 = lerpf(k.r[2].w, k.r[3].w, c.f[0]);
+  const float x01 = lerpf(k.r[4].w, k.r[5].w, c.f[0]), x11 = lerpf(k.r[6].w, k.r[7].w, c.f[0]);
+  const float y0 = lerpf(x00, x10, c.f[1]), y1 = lerpf(x01, x11, c.f[1]);
+  return lerpf(y0, y1, c.f[2]);
+}
+
+// Trilinear blend of the corner gradients (unscaled operator gradient at the sample).
+__device__ __forceinline__ void corners_gradient(const Corners& k, const Cell& c, float g[3]) {
+  const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
+  const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+  const float w[8] = {gx * gy * gz, fx * gy * gz, gx * fy * gz, fx * fy * gz,
+                      gx * gy * fz, fx * gy * fz, gx * fy * fz, fx * fy * fz};
+  float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a = fmaf(w[i], k.r[i].x, a);
+    b = fmaf(w[i], k.r[i].y, b);
+    d = fmaf(w[i], k.r[i].z, d);
+  }
+  g[0] = a;
+  g[1] = b;
+  g[2] = d;
+}
+
+// March one ray with a quad: lane q evaluates sample k + q of every group of four
+// consecutive samples (value, transfer function and, if alpha != 0, gradient and Phong),
+// then every lane composites the group front to back in sample order; the first sample
+// after which 1 - T reaches the threshold ends the ray (later samples of the group are
+// dropped, and counted as not marched).  A group whose samples
+// all lie in invisible bricks jumps to the furthest of their brick exits: every sample in
+// between lies in one of those bricks (each lane's interval starts at its own sample and the
+// starts are consecutive), so nothing visible is skipped.
+template <bool CKPT>
+__device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, bool active,
+                                          int q, unsigned qmask, unsigned& hit, unsigned& plain,
+                                          unsigned& visited, unsigned& shaded) {
+  const int W = L.cam.width, H = L.cam.height;
+  const int ray = py * W + px;
+  const int qbase = (threadIdx.x & 31) & ~3;
+  float o[3], d[3], tn = 0.0f;
+  int K = 0;
+  if (active) ray_setup(L.cam, L.r.lo, L.r.hi, L.r.step, px, py, o, d, tn, K);
+  float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
+  int k = 0;
+  const float step = L.r.step;
+  while (k < K) {
+    const int ks = k + q;
+    const bool live = ks < K;
+    float p[3];
+    const float t = fmaf((float)ks + 0.5f, step, tn);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
+    bool vis = live;
+    int kn = K;
+    if (L.r.skip && live) {
+      int b[3];
+      const int bi = brick_of(L.V, p, b);
+      if (!__ldg(L.V.vis + bi)) {
+        vis = false;
+        kn = brick_exit_sample(b, o, d, tn, step);
+        if (kn <= ks) kn = ks + 1;
+      }
+    }
+    if (((__ballot_sync(qmask, vis) >> qbase) & 0xFu) == 0u) {
+      // the whole group lies in empty bricks: jump
+      kn = max(kn, __shfl_xor_sync(qmask, kn, 1));
+      kn = max(kn, __shfl_xor_sync(qmask, kn, 2));
+      if (CKPT && q == 0) {
+        const int stop = kn < K ? kn : K;
+        for (int j = ((k + kCkptStride - 1) >> 5) << 5; j < stop; j += kCkptStride)
+          if (j > 0) L.ck_T[(size_t)((j >> 5) - 1) * (W * H) + ray] = T;
+      }
+      k = kn;
+      continue;
+    }
+    float alpha = 0.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+    if (vis) {
+      ++visited;
+      const Cell c = cell_of(L.V, p);
+      Corners cr;
+      corners_load(L.R, c, cr);
+      const float s = corners_value(cr, c);
+      const TfSample ts = tf_lookup(L.tf, s);
+      alpha = ts.rgba.w;
+      if (alpha != 0.0f) {
+        ++shaded;
+        float g[3];
+        corners_gradient(cr, c, g);
+        const float gh[3] = {g[0] * L.r.gscale, g[1] * L.r.gscale, g[2] * L.r.gscale};
+        ShadeOut so;
+        shade(L.r.sh, L.cam, d, p, gh, ts.rgba, so);
+        c0 = so.c[0];
+        c1 = so.c[1];
+        c2 = so.c[2];
+      }
+    }
+    // Composite the group in sample order with the sequential recurrence of Eq. 6 (the
+    // same FP32 operations as a one-sample-at-a-time march, so the grouping -- which
+    // shifts after every skip -- never changes a bit of the result).
+    float a4[4], c4[4][3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      a4[j] = __shfl_sync(qmask, alpha, j, 4);
+      c4[j][0] = __shfl_sync(qmask, c0, j, 4);
+      c4[j][1] = __shfl_sync(qmask, c1, j, 4);
+      c4[j][2] = __shfl_sync(qmask, c2, j, 4);
+    }
+    bool stop = false;
+    int used = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!stop && k + j < K) {
+        if (CKPT && q == 0 && k + j > 0 && ((k + j) & (kCkptStride - 1)) == 0)
+          L.ck_T[(size_t)(((k + j) >> 5) - 1) * (W * H) + ray] = T;
+        const float aj = a4[j];
+        if (aj != 0.0f) {
+          const float ta = T * aj;
+          C0 = fmaf(ta, c4[j][0], C0);
+          C1 = fmaf(ta, c4[j][1], C1);
+          C2 = fmaf(ta, c4[j][2], C2);
+          T = T * (1.0f - aj);
+        }
+        used = j + 1;
+        if (1.0f - T >= L.r.ert) stop = true;
+      }
+    }
+    k += used;
+    if (stop) break;
+  }
+  const int kend = k < K ? k : K;
+  if (active && q == 0) {
+    reinterpret_cast<float4*>(L.out)[ray] = make_float4(C0, C1, C2, 1.0f - T);
+    if (CKPT) {
+      L.ck_kend[ray] = kend;
+      L.ck_Tend[ray] = T;
+    }
+    hit += K > 0 ? 1u : 0u;
+    plain += (unsigned)kend;
+  }
+}
+
+}  // namespace vr

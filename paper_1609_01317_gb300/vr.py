@@ -72,6 +72,13 @@ _SIGS = [
     ("vr_render_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                                     C.c_void_p, C.c_int, C.POINTER(vr_camera),
                                     C.POINTER(vr_render_params), C.c_void_p, C.c_void_p]),
+    ("vr_batch_create", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
+                                  C.POINTER(vr_camera), C.POINTER(C.c_int), C.c_int,
+                                  C.POINTER(vr_render_params), C.POINTER(C.c_void_p),
+                                  C.c_void_p]),
+    ("vr_batch_run", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("vr_batch_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    ("vr_batch_destroy", None, [C.c_void_p]),
     ("vr_status_string", C.c_char_p, [C.c_int]),
     ("vr_last_cuda_error", C.c_char_p, []),
     ("vr_version", C.c_int, []),
@@ -210,6 +217,32 @@ def vr_read_stats(ctx, stream=None) -> dict:
     s = vr_stats()
     _check("vr_read_stats", lib().vr_read_stats(ctx, C.byref(s), stream))
     return {k: getattr(s, k) for k, _ in vr_stats._fields_}
+
+
+def vr_batch_create(ctxs, cams, ctx_of_cam, params, outs, stream=None):
+    n = len(cams)
+    h = C.c_void_p()
+    carr = (C.c_void_p * len(ctxs))(*ctxs)
+    cams_arr = (vr_camera * n)(*[c if isinstance(c, vr_camera) else make_camera(c) for c in cams])
+    idx = (C.c_int * n)(*[int(i) for i in ctx_of_cam])
+    oarr = (C.c_void_p * n)(*[_ptr(o) for o in outs])
+    _check("vr_batch_create", lib().vr_batch_create(C.byref(h), carr, len(ctxs), cams_arr, idx, n,
+                                                    C.byref(params), oarr, stream))
+    return h.value
+
+
+def vr_batch_run(batch, stream=None):
+    _check("vr_batch_run", lib().vr_batch_run(batch, stream))
+
+
+def vr_batch_autotune(batch, stream=None):
+    ch = (C.c_int * 3)()
+    _check("vr_batch_autotune", lib().vr_batch_autotune(batch, stream, ch))
+    return tuple(ch)
+
+
+def vr_batch_destroy(batch):
+    lib().vr_batch_destroy(batch)
 
 
 def vr_status_string(status) -> str:

@@ -364,6 +364,34 @@ def workload_ct(width=1920, height=1080, shape=(512, 512, 361), azimuth=0.6, ele
             "grad": "zucker_hummel", "step": 0.5, "skip_empty": True}
 
 
+def workload_batch(scale: float = 1.0, cams_per_volume: int = 64, size: int = 512):
+    """Eight volumes of uneven sizes (uint8 / uint16 alternating, seeds 100..107) with
+    ``cams_per_volume`` seeded orbit cameras each (seeds 200..207) at size x size.
+    ``scale`` shrinks every volume edge (for quick runs).  Transfer functions: two plateaus
+    at the same normalised positions for both storage types."""
+    vols = []
+    for i, (v, vmax) in enumerate(batch_volumes()) if scale == 1.0 else enumerate(
+            _scaled_batch_volumes(scale)):
+        nz, ny, nx = v.shape
+        tf = tf_two_plateau(256, value_max=vmax, soft=(0.2 * vmax, 0.39 * vmax),
+                            bone=(0.54 * vmax, vmax), ramp=0.016 * vmax)
+        cams = seeded_orbit_cameras(200 + i, (nx, ny, nz), cams_per_volume, size, size)
+        vols.append({"volume": v, "value_max": vmax, "tf": tf, "cameras": cams})
+    return vols
+
+
+def _scaled_batch_volumes(scale: float, seed0: int = 100):
+    sizes = [(96, 96, 96), (128, 128, 128), (160, 200, 120), (256, 256, 256),
+             (300, 300, 200), (320, 320, 320), (384, 384, 384), (384, 384, 256)]
+    out = []
+    for i, shp in enumerate(sizes):
+        shp = tuple(max(8, int(round(s * scale))) for s in shp)
+        vmax = U8_MAX if i % 2 == 0 else U12_MAX
+        dt = np.uint8 if i % 2 == 0 else np.uint16
+        out.append((ellipsoids(seed0 + i, shp, value_max=vmax, dtype=dt), vmax))
+    return out
+
+
 def training_views(n: int = 128, width: int = 256, height: int = 256):
     """Sixteen views of an n^3 volume: 6 axis + 2 diagonal orthographic, 8 perspective orbits."""
     shp = (n, n, n)
