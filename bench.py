@@ -29,9 +29,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic FP32 operations per sample (see the design notes): every visited sample
-# pays the trilinear value, the transfer-function lerp and the sample position; a shaded
-# sample adds the operator gradient (blended over the cell), the normalisation, Phong and
+# Algorithmic FP32 operations per sample (fused multiply-add = 2): every visited sample
+# pays its position, the cell fractions, the trilinear value (7 lerps) and the opacity
+# lerp; a shaded sample adds the colour lerps, the operator gradient contracted from the
+# cell's neighbourhood with the trilinear weights (the per-sample form that needs no
+# precomputed state: the 32-voxel cross for central differences, the separable 4x4x4
+# contraction for Sobel3D and Zucker-Hummel), the normalisation, Phong with its power and
 # the compositing update.
 FLOPS_VISIT = 34
 FLOPS_SHADE = {"central": 96, "sobel3d": 392, "zucker_hummel": 392}
@@ -48,6 +51,10 @@ def parse():
     ap.add_argument("--workload", choices=["ct", "ellipsoids", "sphere"], default="ct")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch"], default="main",
+                    help="run one leg alone and print its JSON (for profiling)")
+    ap.add_argument("--source-hash", choices=sorted(KERNEL_SOURCES),
+                    help="print the source hash recorded beside a kernel's ncu counters")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="edge scale of the batched-render volumes (1.0 = full sizes)")
     return ap.parse_args()
@@ -93,8 +100,13 @@ class ClockSampler:
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
+            # the first query can take a while: start timing only once the sampler runs
+            t0 = time.perf_counter()
+            while os.path.getsize(self.path) == 0 and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
+            self.skip = sum(1 for _ in open(self.path))
         except Exception:
             self.proc = None
         return self
@@ -113,7 +125,9 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
         try:
-            for line in open(self.path):
+            for i, line in enumerate(open(self.path)):
+                if i < getattr(self, "skip", 0):
+                    continue  # taken before the timed region started
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) >= 9:
                     rows.append(parts)
@@ -157,26 +171,72 @@ def barrier(world):
     torch.cuda.synchronize()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    import torch.distributed as dist
+
+    return _reduce(x, world, dist.ReduceOp.MAX) if world > 1 else x
 
 
 def sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM) if world > 1 else x
+
+
+def replica_throughput(samples_per_step, steps, step_ms_total, world):
+    """Whole-job throughput of N independent replicas (weak scaling): the samples of all
+    ranks divided by the slowest rank's time.  Returns (Gsamples/s, ms per step)."""
+    total_ms = max_over_ranks(step_ms_total, world)
+    samples = sum_over_ranks(float(samples_per_step) * steps, world)
+    return samples / (total_ms / 1e3) / 1e9, total_ms / steps
+
+
+# ------------------------------------------------------------ ncu traffic record
+KERNEL_SOURCES = {
+    "k_march": ["vr_device.cuh", "vr_march.cuh", "vr_render.cu"],
+    "k_adjoint": ["vr_device.cuh", "vr_adjoint.cu"],
+}
+PROFILE_SUMMARY = {"k_march": "profiles/k_march_ct512x512x361_1080p.md",
+                   "k_adjoint": "profiles/k_adjoint_density128_16views.md"}
+
+
+def source_hash(kernel):
+    """SHA-256 over the sources a kernel is built from (recorded beside its ncu counters)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1609_01317_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes (read + write) per launch from the committed ncu summary of `kernel`, or
+    None when there is none or the kernel's sources changed since the capture."""
+    try:
+        fields = {}
+        for line in open(os.path.join(ROOT, PROFILE_SUMMARY[kernel])):
+            if ":" in line and line.lstrip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("source_sha256") != source_hash(kernel):
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -456,13 +516,13 @@ def run_ours(args):
         evr[i][1].record(stream)
     torch.cuda.synchronize()
     march_ms = [evr[i][0].elapsed_time(evr[i][1]) for i in range(K)]
-    total_ms = max_over_ranks(sum(step_ms), world)
     samples = stats["samples_plain"]
-    value = sum_over_ranks(samples * K, world) / (total_ms / 1e3) / 1e9
-    ms_per_step = total_ms / K
+    value, ms_per_step = replica_throughput(samples, K, sum(step_ms), world)
     march_avg = statistics.mean(march_ms)
 
-    # roofline of the dominant kernel (the fused march)
+    # roofline of the dominant kernel (the fused march): FP32 ALU against the unit counts
+    # and the maximum SM clock; algorithmic operations per visited / shaded sample as
+    # defined by FLOPS_VISIT / FLOPS_SHADE
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
@@ -471,11 +531,16 @@ def run_ours(args):
     bpv = {"u8": 1, "u16": 2, "f16": 2, "f32": 4}[dt]
     hbm_bytes = (nx + 3) * (ny + 3) * (nz + 3) * bpv + H * W * 16
     hbm_achieved = hbm_bytes / (march_avg / 1e3) / 1e9
+    records_ms = max(render_ms - march_avg, 0.0)
     roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": achieved / alu_peak, "traffic": None,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+            "frac": achieved / alu_peak, "traffic": profiled_traffic("k_march"),
+            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+            "kernel": "k_march", "launch_ms": march_avg,
+            "flops_per_launch": flops,
+            "frac_incl_records": flops / ((march_avg + records_ms) / 1e3) / 1e12 / alu_peak}
     roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": float(pk["hbm_gbs"]),
                 "unit": "GB/s", "frac": hbm_achieved / float(pk["hbm_gbs"]),
+                "bytes_per_launch": hbm_bytes,
                 "peak_source": f"{pk_kind} copy bandwidth"}
 
     line = {
@@ -490,7 +555,7 @@ def run_ours(args):
                    "parallelism": f"replicas{world}"},
         "frames_per_s": 1000.0 / ms_per_step,
         "phase_ms": {"upload": upload_ms, "tf_camera": tf_ms, "render": render_ms,
-                     "records": render_ms - march_avg, "march": march_avg},
+                     "records": records_ms, "march": march_avg},
         "render_only": {"value": samples / (march_avg / 1e3) / 1e9, "unit": "Gsamples/s",
                         "frames_per_s": 1000.0 / march_avg},
         "march_ms": march_avg,
@@ -555,8 +620,30 @@ def run_ours(args):
     return 0
 
 
+def run_leg(args):
+    import torch
+
+    from paper_1609_01317_gb300 import Renderer, build
+
+    build.build()
+    torch.cuda.set_device(0)
+    if args.leg == "fwd_bwd":
+        R = Renderer(0)
+        out = fwd_bwd_leg(R, args)
+        R.close()
+    else:
+        out = batch_leg(args)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.source_hash:
+        print(source_hash(args.source_hash))
+        return 0
+    if args.leg != "main":
+        return run_leg(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
