@@ -90,16 +90,64 @@ __device__ __noinline__ float recompute_T(const AdjointLaunch& L, const float o[
 }
 
 
+// Sums v[0..7] over every group of lanes that share `peers` (a __match_any_sync result)
+// into the group's lowest lane: a tree over the lanes' ranks within their group.  Every
+// lane of the warp calls it.
+__device__ __forceinline__ void peer_sum(unsigned peers, int lane, float v[8]) {
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  unsigned rest = peers & ~((2u << lane) - 1u);  // the group's lanes above this one
+  const int top = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
+  for (int s = 1; s < top; s <<= 1) {
+    // rest's lowest bit is the lane of rank + s
+    const int src = rest ? __ffs(rest) - 1 : lane;
+    const bool take = rest != 0u && (rank & (2 * s - 1)) == 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float t = __shfl_sync(0xffffffffu, v[j], src);
+      if (take) v[j] += t;
+    }
+    for (int c = 0; c < s && rest; ++c) rest &= rest - 1u;
+  }
+}
+
+// Adds the transfer-function run sums of the lanes where `pred` holds (lo to entry idx, hi
+// to entry idx + 1) to the warp's private table in shared memory, without atomics: lanes
+// with the same idx are summed first, so in each of the two phases the lanes that write
+// touch distinct entries.  Every lane of the warp calls it.
+__device__ __forceinline__ void warp_flush_tf(float* table, bool pred, int idx, const float lo[4],
+                                              const float hi[4], int lane) {
+  const unsigned key = pred ? (unsigned)idx : (0x80000000u | (unsigned)lane);
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  float v[8] = {lo[0], lo[1], lo[2], lo[3], hi[0], hi[1], hi[2], hi[3]};
+  peer_sum(peers, lane, v);
+  const bool lead = pred && (__ffs(peers) - 1) == lane;
+  float4* e = reinterpret_cast<float4*>(table) + (lead ? idx : 0);
+  if (lead) {
+    float4 t = e[0];
+    t.x += v[0]; t.y += v[1]; t.z += v[2]; t.w += v[3];
+    e[0] = t;
+  }
+  __syncwarp();
+  if (lead) {
+    float4 t = e[1];
+    t.x += v[4]; t.y += v[5]; t.z += v[6]; t.w += v[7];
+    e[1] = t;
+  }
+  __syncwarp();
+}
+
 // Four lanes per ray: lane q takes sample kg + q of every group of four, groups visited from
 // the last to the first.  Per group: the transmittances before each sample come from the
 // transmittance after the group divided by the product of (1 - alpha) over it (exactly
 // re-anchored at every 32-sample checkpoint), and the adjoint of the transmittance follows
-// from a suffix scan of the affine maps Tadj -> alpha g.c + (1 - alpha) Tadj.
+// from a suffix scan of the affine maps Tadj -> alpha g.c + (1 - alpha) Tadj.  The group loop
+// runs the same number of times on every lane of the warp (quads whose ray is done idle), so
+// that the transfer-function sums can be combined across the warp.
 __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
   // TF contributions: summed in registers per run of samples that read the same pair of
-  // entries, flushed into a per-warp table in shared memory (tables up to kMaxWarpTf
-  // entries; larger ones go to global memory), which the warp adds to the global result
-  // when it runs out of tiles -- no block-wide barrier.
+  // entries; a lane whose run ends hands it to the warp, which adds the runs to a per-warp
+  // table in shared memory (tables up to kMaxWarpTf entries; larger ones take global
+  // atomics) and adds the table to the global result when it runs out of tiles.
   extern __shared__ float smem[];
   const int tid = threadIdx.x;
   const bool warp_tf = L.grad_tf && L.tf.n <= kMaxWarpTf;
@@ -138,143 +186,167 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
       Tcur = L.ck_Tend[ray];
     }
     float Tadj = -gr.w;
+    const int ng = kend > 0 ? ((kend - 1) >> 2) + 1 : 0;  // groups of this quad's ray
+    const int maxg = (int)__reduce_max_sync(0xffffffffu, (unsigned)ng);
     int tf_run = -1;
     float tf_lo[4] = {0.f, 0.f, 0.f, 0.f}, tf_hi[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int kg = ((kend - 1) >> 2) << 2; kend > 0 && kg >= 0; kg -= 4) {
-      const int k = kg + q;
-      const bool live = k < kend;
-      float alpha = 0.0f, gc = 0.0f;
-      float p[3];
-      AdjCell c;
-      float4 r[8];
-      TfSample ts;
-      ShadeOut so;
-      float gh[3] = {0.f, 0.f, 0.f};
-      if (live) {
-        const float t = fmaf((float)k + 0.5f, step, tn);
+    for (int it = 0; it < maxg; ++it) {
+      bool contrib = false;
+      int ci = 0;
+      float cw = 0.0f;
+      float drgba[4] = {0.f, 0.f, 0.f, 0.f};
+      if (it < ng) {
+        const int kg = (ng - 1 - it) << 2;
+        const int k = kg + q;
+        const bool live = k < kend;
+        float alpha = 0.0f, gc = 0.0f;
+        float p[3];
+        AdjCell c;
+        float4 r[8];
+        TfSample ts;
+        ShadeOut so;
+        float gh[3] = {0.f, 0.f, 0.f};
+        if (live) {
+          const float t = fmaf((float)k + 0.5f, step, tn);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
-        c = adj_cell(L.V, p);
-        ts = tf_lookup(L.tf, record_value(L.R, c, r));
-        float g[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float wci = corner_weight(c.f, i);
-          g[0] = fmaf(wci, r[i].x, g[0]);
-          g[1] = fmaf(wci, r[i].y, g[1]);
-          g[2] = fmaf(wci, r[i].z, g[2]);
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gh[a] = g[a] * gs;
-        shade(L.r.sh, L.cam, d, p, gh, ts.rgba, so);
-        alpha = ts.rgba.w;
-        gc = gr.x * so.c[0] + gr.y * so.c[1] + gr.z * so.c[2];
-      }
-      // transmittances: exclusive / inclusive prefix products of (1 - alpha) over the group
-      const float om = 1.0f - alpha;
-      float P = om;
-      float u = __shfl_up_sync(qmask, P, 1, 4);
-      if (q >= 1) P *= u;
-      u = __shfl_up_sync(qmask, P, 2, 4);
-      if (q >= 2) P *= u;
-      float E = __shfl_up_sync(qmask, P, 1, 4);
-      if (q == 0) E = 1.0f;
-      const float prod = __shfl_sync(qmask, P, 3, 4);
-      float Tb;
-      if (kg == 0) Tb = 1.0f;
-      else if ((kg & (kCkptStride - 1)) == 0) Tb = L.ck_T[(size_t)((kg >> 5) - 1) * nrays + ray];
-      else if (prod > 1e-4f) Tb = Tcur / prod;
-      else Tb = recompute_T(L, o, d, tn, kg, ray);
-      const float Tk = Tb * E;
-      // adjoint of T: suffix scan of x -> A + B x over the group
-      float A = alpha * gc, B = om;
-      float An = __shfl_down_sync(qmask, A, 1, 4), Bn = __shfl_down_sync(qmask, B, 1, 4);
-      if (q <= 2) {
-        A = fmaf(B, An, A);
-        B = B * Bn;
-      }
-      An = __shfl_down_sync(qmask, A, 2, 4);
-      Bn = __shfl_down_sync(qmask, B, 2, 4);
-      if (q <= 1) {
-        A = fmaf(B, An, A);
-        B = B * Bn;
-      }
-      float Ae = __shfl_down_sync(qmask, A, 1, 4), Be = __shfl_down_sync(qmask, B, 1, 4);
-      if (q == 3) {
-        Ae = 0.0f;
-        Be = 1.0f;
-      }
-      const float Tadj_next = fmaf(Be, Tadj, Ae);  // adjoint of T after this lane's sample
-      const float A0 = __shfl_sync(qmask, A, 0, 4), B0 = __shfl_sync(qmask, B, 0, 4);
-      if (live) {
-        const float dalpha = Tk * (gc - Tadj_next);
-        const float ta = Tk * alpha;
-        const float dc[3] = {ta * gr.x, ta * gr.y, ta * gr.z};
-        // Phong backward: c = rgb (ka + kd diff) + ks spec
-        const float diff = fmaxf(so.nl, 0.0f);
-        const float kk = fmaf(L.r.sh.kd, diff, L.r.sh.ka);
-        float drgba[4] = {dc[0] * kk, dc[1] * kk, dc[2] * kk, dalpha};
-        float dN[3] = {0.f, 0.f, 0.f};
-        if (so.nl > 0.0f) {
-          const float d_diff = L.r.sh.kd * (dc[0] * ts.rgba.x + dc[1] * ts.rgba.y + dc[2] * ts.rgba.z);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) dN[a] = d_diff * so.L[a];
-          if (so.rv > 0.0f && L.r.sh.shininess != 0.0f) {
-            const float d_spec = L.r.sh.ks * (dc[0] + dc[1] + dc[2]);
-            const float dx = d_spec * L.r.sh.shininess * __powf(so.rv, L.r.sh.shininess - 1.0f);
-            const float nv = so.N[0] * so.V[0] + so.N[1] * so.V[1] + so.N[2] * so.V[2];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) dN[a] += dx * 2.0f * (nv * so.L[a] + so.nl * so.V[a]);
-          }
-        }
-        // normal backward: N = -g_hat / |g_hat|, then to the unscaled operator gradient
-        float dg[3] = {0.f, 0.f, 0.f};
-        if (so.gl * so.gl > 1e-12f && so.gl > 0.0f) {
-          const float il = 1.0f / so.gl;
-          const float nh[3] = {gh[0] * il, gh[1] * il, gh[2] * il};
-          const float dn = dN[0] * nh[0] + dN[1] * nh[1] + dN[2] * nh[2];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) dg[a] = -(dN[a] - dn * nh[a]) * il * gs;
-        }
-        // transfer-function backward
-        float ds = 0.0f;
-        {
-          const int i = ts.i;
-          const float wt = ts.w;
-          if (ts.inside) {
-            const float4 ta4 = __ldg(L.tf.tf + i), tb4 = __ldg(L.tf.tf + i + 1);
-            ds = (drgba[0] * (tb4.x - ta4.x) + drgba[1] * (tb4.y - ta4.y) +
-                  drgba[2] * (tb4.z - ta4.z) + drgba[3] * (tb4.w - ta4.w)) * L.tf.scale;
-          }
-          if (L.grad_tf) {
-            if (i != tf_run) {
-              if (tf_run >= 0) flush_tf(tf_dst, tf_run, tf_lo, tf_hi);
-              tf_run = i;
-#pragma unroll
-              for (int j = 0; j < 4; ++j) tf_lo[j] = tf_hi[j] = 0.0f;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              tf_lo[j] = fmaf(1.0f - wt, drgba[j], tf_lo[j]);
-              tf_hi[j] = fmaf(wt, drgba[j], tf_hi[j]);
-            }
-          }
-        }
-        // scatter (dL/dV direct, dL/dG) to the cell corners
-        if (L.adj && (ds != 0.0f || dg[0] != 0.0f || dg[1] != 0.0f || dg[2] != 0.0f)) {
+          for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
+          c = adj_cell(L.V, p);
+          ts = tf_lookup(L.tf, record_value(L.R, c, r));
+          float g[3] = {0.f, 0.f, 0.f};
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const float wci = corner_weight(c.f, i);
-            atomicAdd(L.adj + corner_index(L.R, c.base, i),
-                      make_float4(wci * ds, wci * dg[0], wci * dg[1], wci * dg[2]));
+            g[0] = fmaf(wci, r[i].x, g[0]);
+            g[1] = fmaf(wci, r[i].y, g[1]);
+            g[2] = fmaf(wci, r[i].z, g[2]);
+          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) gh[a] = g[a] * gs;
+          shade(L.r.sh, L.cam, d, p, gh, ts.rgba, so);
+          alpha = ts.rgba.w;
+          gc = gr.x * so.c[0] + gr.y * so.c[1] + gr.z * so.c[2];
+        }
+        // transmittances: exclusive / inclusive prefix products of (1 - alpha) over the group
+        const float om = 1.0f - alpha;
+        float P = om;
+        float u = __shfl_up_sync(qmask, P, 1, 4);
+        if (q >= 1) P *= u;
+        u = __shfl_up_sync(qmask, P, 2, 4);
+        if (q >= 2) P *= u;
+        float E = __shfl_up_sync(qmask, P, 1, 4);
+        if (q == 0) E = 1.0f;
+        const float prod = __shfl_sync(qmask, P, 3, 4);
+        float Tb;
+        if (kg == 0) Tb = 1.0f;
+        else if ((kg & (kCkptStride - 1)) == 0) Tb = L.ck_T[(size_t)((kg >> 5) - 1) * nrays + ray];
+        else if (prod > 1e-4f) Tb = Tcur / prod;
+        else Tb = recompute_T(L, o, d, tn, kg, ray);
+        const float Tk = Tb * E;
+        // adjoint of T: suffix scan of x -> A + B x over the group
+        float A = alpha * gc, B = om;
+        float An = __shfl_down_sync(qmask, A, 1, 4), Bn = __shfl_down_sync(qmask, B, 1, 4);
+        if (q <= 2) {
+          A = fmaf(B, An, A);
+          B = B * Bn;
+        }
+        An = __shfl_down_sync(qmask, A, 2, 4);
+        Bn = __shfl_down_sync(qmask, B, 2, 4);
+        if (q <= 1) {
+          A = fmaf(B, An, A);
+          B = B * Bn;
+        }
+        float Ae = __shfl_down_sync(qmask, A, 1, 4), Be = __shfl_down_sync(qmask, B, 1, 4);
+        if (q == 3) {
+          Ae = 0.0f;
+          Be = 1.0f;
+        }
+        const float Tadj_next = fmaf(Be, Tadj, Ae);  // adjoint of T after this lane's sample
+        const float A0 = __shfl_sync(qmask, A, 0, 4), B0 = __shfl_sync(qmask, B, 0, 4);
+        if (live) {
+          const float dalpha = Tk * (gc - Tadj_next);
+          const float ta = Tk * alpha;
+          const float dc[3] = {ta * gr.x, ta * gr.y, ta * gr.z};
+          // Phong backward: c = rgb (ka + kd diff) + ks spec
+          const float diff = fmaxf(so.nl, 0.0f);
+          const float kk = fmaf(L.r.sh.kd, diff, L.r.sh.ka);
+          drgba[0] = dc[0] * kk;
+          drgba[1] = dc[1] * kk;
+          drgba[2] = dc[2] * kk;
+          drgba[3] = dalpha;
+          float dN[3] = {0.f, 0.f, 0.f};
+          if (so.nl > 0.0f) {
+            const float d_diff = L.r.sh.kd * (dc[0] * ts.rgba.x + dc[1] * ts.rgba.y + dc[2] * ts.rgba.z);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dN[a] = d_diff * so.L[a];
+            if (so.rv > 0.0f && L.r.sh.shininess != 0.0f) {
+              const float d_spec = L.r.sh.ks * (dc[0] + dc[1] + dc[2]);
+              const float dx = d_spec * L.r.sh.shininess * __powf(so.rv, L.r.sh.shininess - 1.0f);
+              const float nv = so.N[0] * so.V[0] + so.N[1] * so.V[1] + so.N[2] * so.V[2];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) dN[a] += dx * 2.0f * (nv * so.L[a] + so.nl * so.V[a]);
+            }
+          }
+          // normal backward: N = -g_hat / |g_hat|, then to the unscaled operator gradient
+          float dg[3] = {0.f, 0.f, 0.f};
+          if (so.gl * so.gl > 1e-12f && so.gl > 0.0f) {
+            const float il = 1.0f / so.gl;
+            const float nh[3] = {gh[0] * il, gh[1] * il, gh[2] * il};
+            const float dn = dN[0] * nh[0] + dN[1] * nh[1] + dN[2] * nh[2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dg[a] = -(dN[a] - dn * nh[a]) * il * gs;
+          }
+          // transfer-function backward: the slope to the value here, the entries below
+          float ds = 0.0f;
+          if (ts.inside) {
+            const float4 ta4 = __ldg(L.tf.tf + ts.i), tb4 = __ldg(L.tf.tf + ts.i + 1);
+            ds = (drgba[0] * (tb4.x - ta4.x) + drgba[1] * (tb4.y - ta4.y) +
+                  drgba[2] * (tb4.z - ta4.z) + drgba[3] * (tb4.w - ta4.w)) * L.tf.scale;
+          }
+          contrib = L.grad_tf != nullptr;
+          ci = ts.i;
+          cw = ts.w;
+          // scatter (dL/dV direct, dL/dG) to the cell corners
+          if (L.adj && (ds != 0.0f || dg[0] != 0.0f || dg[1] != 0.0f || dg[2] != 0.0f)) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float wci = corner_weight(c.f, i);
+              atomicAdd(L.adj + corner_index(L.R, c.base, i),
+                        make_float4(wci * ds, wci * dg[0], wci * dg[1], wci * dg[2]));
+            }
+          }
+        }
+        Tcur = Tb;
+        Tadj = fmaf(B0, Tadj, A0);
+      }
+      if (L.grad_tf) {
+        const bool change = contrib && tf_run >= 0 && ci != tf_run;
+        if (warp_tf) {
+          if (__any_sync(0xffffffffu, change)) warp_flush_tf(tf_dst, change, tf_run, tf_lo, tf_hi, lane);
+        } else if (change) {
+          flush_tf(tf_dst, tf_run, tf_lo, tf_hi);
+        }
+        if (contrib) {
+          if (ci != tf_run) {
+            tf_run = ci;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tf_lo[j] = tf_hi[j] = 0.0f;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            tf_lo[j] = fmaf(1.0f - cw, drgba[j], tf_lo[j]);
+            tf_hi[j] = fmaf(cw, drgba[j], tf_hi[j]);
           }
         }
       }
-      Tcur = Tb;
-      Tadj = fmaf(B0, Tadj, A0);
     }
-    if (L.grad_tf && tf_run >= 0) flush_tf(tf_dst, tf_run, tf_lo, tf_hi);
-    __syncwarp();
+    if (L.grad_tf) {
+      const bool pend = tf_run >= 0;
+      if (warp_tf) {
+        if (__any_sync(0xffffffffu, pend)) warp_flush_tf(tf_dst, pend, tf_run, tf_lo, tf_hi, lane);
+      } else if (pend) {
+        flush_tf(tf_dst, tf_run, tf_lo, tf_hi);
+      }
+    }
   }
   if (warp_tf) {
     __syncwarp();
