@@ -21,7 +21,7 @@
 namespace vr {
 
 constexpr int kThreads = 128;
-constexpr int kMaxWarpTf = 512;  // per-warp shared TF tables up to this many entries
+constexpr int kMaxTfRows = 4096;  // per-block partial rows of the TF gradient up to this many entries
 constexpr int kQuadTileW = 4, kQuadTileH = 2;  // pixels per warp (a quad of lanes per ray)
 
 // Corner records of a cell and the trilinear weights of the sample in it.
@@ -90,50 +90,14 @@ __device__ __noinline__ float recompute_T(const AdjointLaunch& L, const float o[
 }
 
 
-// Sums v[0..7] over every group of lanes that share `peers` (a __match_any_sync result)
-// into the group's lowest lane: a tree over the lanes' ranks within their group.  Every
-// lane of the warp calls it.
-__device__ __forceinline__ void peer_sum(unsigned peers, int lane, float v[8]) {
-  const int rank = __popc(peers & ((1u << lane) - 1u));
-  unsigned rest = peers & ~((2u << lane) - 1u);  // the group's lanes above this one
-  const int top = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
-  for (int s = 1; s < top; s <<= 1) {
-    // rest's lowest bit is the lane of rank + s
-    const int src = rest ? __ffs(rest) - 1 : lane;
-    const bool take = rest != 0u && (rank & (2 * s - 1)) == 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float t = __shfl_sync(0xffffffffu, v[j], src);
-      if (take) v[j] += t;
-    }
-    for (int c = 0; c < s && rest; ++c) rest &= rest - 1u;
-  }
-}
-
-// Adds the transfer-function run sums of the lanes where `pred` holds (lo to entry idx, hi
-// to entry idx + 1) to the warp's private table in shared memory, without atomics: lanes
-// with the same idx are summed first, so in each of the two phases the lanes that write
-// touch distinct entries.  Every lane of the warp calls it.
-__device__ __forceinline__ void warp_flush_tf(float* table, bool pred, int idx, const float lo[4],
-                                              const float hi[4], int lane) {
-  const unsigned key = pred ? (unsigned)idx : (0x80000000u | (unsigned)lane);
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  float v[8] = {lo[0], lo[1], lo[2], lo[3], hi[0], hi[1], hi[2], hi[3]};
-  peer_sum(peers, lane, v);
-  const bool lead = pred && (__ffs(peers) - 1) == lane;
-  float4* e = reinterpret_cast<float4*>(table) + (lead ? idx : 0);
-  if (lead) {
-    float4 t = e[0];
-    t.x += v[0]; t.y += v[1]; t.z += v[2]; t.w += v[3];
-    e[0] = t;
-  }
-  __syncwarp();
-  if (lead) {
-    float4 t = e[1];
-    t.x += v[4]; t.y += v[5]; t.z += v[6]; t.w += v[7];
-    e[1] = t;
-  }
-  __syncwarp();
+// Adds a finished run of the transfer-function gradient (lo to entry i, hi to entry i + 1)
+// to the block's row of the partial sums with two vector reductions.
+__device__ __forceinline__ void flush_tf_row(float* row, int i, const float lo[4], const float hi[4]) {
+  float4* e = reinterpret_cast<float4*>(row) + i;
+  if (lo[0] != 0.0f || lo[1] != 0.0f || lo[2] != 0.0f || lo[3] != 0.0f)
+    atomicAdd(e, make_float4(lo[0], lo[1], lo[2], lo[3]));
+  if (hi[0] != 0.0f || hi[1] != 0.0f || hi[2] != 0.0f || hi[3] != 0.0f)
+    atomicAdd(e + 1, make_float4(hi[0], hi[1], hi[2], hi[3]));
 }
 
 // Four lanes per ray: lane q takes sample kg + q of every group of four, groups visited from
@@ -141,20 +105,14 @@ __device__ __forceinline__ void warp_flush_tf(float* table, bool pred, int idx, 
 // transmittance after the group divided by the product of (1 - alpha) over it (exactly
 // re-anchored at every 32-sample checkpoint), and the adjoint of the transmittance follows
 // from a suffix scan of the affine maps Tadj -> alpha g.c + (1 - alpha) Tadj.  The group loop
-// runs the same number of times on every lane of the warp (quads whose ray is done idle), so
-// that the transfer-function sums can be combined across the warp.
+// runs the same number of times on every lane of the warp (quads whose ray is done idle).
 __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
   // TF contributions: summed in registers per run of samples that read the same pair of
-  // entries; a lane whose run ends hands it to the warp, which adds the runs to a per-warp
-  // table in shared memory (tables up to kMaxWarpTf entries; larger ones take global
-  // atomics) and adds the table to the global result when it runs out of tiles.
-  extern __shared__ float smem[];
+  // entries; a finished run goes to this block's row of the partial sums in global memory
+  // (vector reductions, no contention between blocks), or, without a partial-sum buffer,
+  // straight to grad_tf with scalar atomics.
   const int tid = threadIdx.x;
-  const bool warp_tf = L.grad_tf && L.tf.n <= kMaxWarpTf;
-  float* tf_dst = warp_tf ? smem + (tid >> 5) * 4 * L.tf.n : L.grad_tf;
-  if (warp_tf)
-    for (int i = (tid & 31); i < 4 * L.tf.n; i += 32) tf_dst[i] = 0.0f;
-  __syncwarp();
+  float* tf_row = L.tf_partial ? L.tf_partial + (size_t)blockIdx.x * 4 * L.tf.n : nullptr;
 
   const int lane = tid & 31, q = lane & 3, qd = lane >> 2;
   const unsigned qmask = 0xFu << (lane & ~3);
@@ -206,6 +164,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
         TfSample ts;
         ShadeOut so;
         float gh[3] = {0.f, 0.f, 0.f};
+        float sv[4] = {0.f, 0.f, 0.f, 0.f};  // (dL/ds, dL/dG) of this sample
+        bool scat = false;
         if (live) {
           const float t = fmaf((float)k + 0.5f, step, tn);
 #pragma unroll
@@ -305,71 +265,98 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
           contrib = L.grad_tf != nullptr;
           ci = ts.i;
           cw = ts.w;
-          // scatter (dL/dV direct, dL/dG) to the cell corners
-          if (L.adj && (ds != 0.0f || dg[0] != 0.0f || dg[1] != 0.0f || dg[2] != 0.0f)) {
+          sv[0] = ds;
+          sv[1] = dg[0];
+          sv[2] = dg[1];
+          sv[3] = dg[2];
+          scat = L.adj && (ds != 0.0f || dg[0] != 0.0f || dg[1] != 0.0f || dg[2] != 0.0f);
+        }
+        // scatter (dL/dV direct, dL/dG) to the cell corners; two neighbouring samples of
+        // the ray (lanes q, q ^ 1) in the same cell are scattered together by the even lane
+        {
+          const unsigned cb_lo = scat ? (unsigned)c.base : 0xffffffffu;
+          const unsigned cb_hi = scat ? (unsigned)(c.base >> 32) : 0xffffffffu;
+          const unsigned pb_lo = __shfl_xor_sync(qmask, cb_lo, 1, 4);
+          const unsigned pb_hi = __shfl_xor_sync(qmask, cb_hi, 1, 4);
+          const bool pscat = __shfl_xor_sync(qmask, (int)scat, 1, 4) != 0;
+          float pf[3], pv[4];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) pf[a] = __shfl_xor_sync(qmask, scat ? c.f[a] : 0.0f, 1, 4);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) pv[a] = __shfl_xor_sync(qmask, sv[a], 1, 4);
+          const bool same = scat && pscat && pb_lo == cb_lo && pb_hi == cb_hi;
+          if (scat && !(same && (q & 1))) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const float wci = corner_weight(c.f, i);
-              atomicAdd(L.adj + corner_index(L.R, c.base, i),
-                        make_float4(wci * ds, wci * dg[0], wci * dg[1], wci * dg[2]));
+              float4 v = make_float4(wci * sv[0], wci * sv[1], wci * sv[2], wci * sv[3]);
+              if (same) {
+                const float wpi = corner_weight(pf, i);
+                v.x = fmaf(wpi, pv[0], v.x);
+                v.y = fmaf(wpi, pv[1], v.y);
+                v.z = fmaf(wpi, pv[2], v.z);
+                v.w = fmaf(wpi, pv[3], v.w);
+              }
+              atomicAdd(L.adj + corner_index(L.R, c.base, i), v);
             }
           }
         }
         Tcur = Tb;
         Tadj = fmaf(B0, Tadj, A0);
       }
-      if (L.grad_tf) {
-        const bool change = contrib && tf_run >= 0 && ci != tf_run;
-        if (warp_tf) {
-          if (__any_sync(0xffffffffu, change)) warp_flush_tf(tf_dst, change, tf_run, tf_lo, tf_hi, lane);
-        } else if (change) {
-          flush_tf(tf_dst, tf_run, tf_lo, tf_hi);
+      if (contrib) {
+        if (ci != tf_run) {
+          if (tf_run >= 0) {
+            if (tf_row) flush_tf_row(tf_row, tf_run, tf_lo, tf_hi);
+            else flush_tf(L.grad_tf, tf_run, tf_lo, tf_hi);
+          }
+          tf_run = ci;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tf_lo[j] = tf_hi[j] = 0.0f;
         }
-        if (contrib) {
-          if (ci != tf_run) {
-            tf_run = ci;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) tf_lo[j] = tf_hi[j] = 0.0f;
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            tf_lo[j] = fmaf(1.0f - cw, drgba[j], tf_lo[j]);
-            tf_hi[j] = fmaf(cw, drgba[j], tf_hi[j]);
-          }
+        for (int j = 0; j < 4; ++j) {
+          tf_lo[j] = fmaf(1.0f - cw, drgba[j], tf_lo[j]);
+          tf_hi[j] = fmaf(cw, drgba[j], tf_hi[j]);
         }
       }
     }
-    if (L.grad_tf) {
-      const bool pend = tf_run >= 0;
-      if (warp_tf) {
-        if (__any_sync(0xffffffffu, pend)) warp_flush_tf(tf_dst, pend, tf_run, tf_lo, tf_hi, lane);
-      } else if (pend) {
-        flush_tf(tf_dst, tf_run, tf_lo, tf_hi);
-      }
-    }
-  }
-  if (warp_tf) {
-    __syncwarp();
-    for (int i = (tid & 31); i < 4 * L.tf.n; i += 32) {
-      const float v = tf_dst[i];
-      if (v != 0.0f) atomicAdd(L.grad_tf + i, v);
+    if (tf_run >= 0) {
+      if (tf_row) flush_tf_row(tf_row, tf_run, tf_lo, tf_hi);
+      else flush_tf(L.grad_tf, tf_run, tf_lo, tf_hi);
     }
   }
 }
 
-static int adjoint_blocks(size_t smem) {
+__global__ void k_tf_partial_reduce(const float* __restrict__ partial, int blocks, int n4,
+                                    float* __restrict__ grad_tf) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n4) return;
+  float v = 0.0f;
+  for (int b = 0; b < blocks; ++b) v += partial[(size_t)b * n4 + e];
+  grad_tf[e] += v;
+}
+
+cudaError_t launch_tf_partial_reduce(const float* partial, int blocks, int n4, float* grad_tf,
+                                     cudaStream_t s) {
+  k_tf_partial_reduce<<<(n4 + 127) / 128, 128, 0, s>>>(partial, blocks, n4, grad_tf);
+  return cudaGetLastError();
+}
+
+bool adjoint_tf_rows(int ntf) { return ntf <= kMaxTfRows; }
+
+int adjoint_grid() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint, kThreads, 0);
   return (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
 }
 
 cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t s) {
-  const size_t smem = (L.grad_tf && L.tf.n <= kMaxWarpTf) ? sizeof(float) * 4 * L.tf.n * (kThreads / 32) : 0;
   cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  k_adjoint<<<adjoint_blocks(smem), kThreads, smem, s>>>(L);
+  k_adjoint<<<adjoint_grid(), kThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 

@@ -351,6 +351,7 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->stats);
   ctx_free(ctx, ctx->out_staging);
   ctx_free(ctx, ctx->adj);
+  ctx_free(ctx, ctx->tf_partial);
   ctx_free(ctx, ctx->rec);
   delete ctx;
 }
@@ -570,6 +571,18 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
     st = cuda_status(cudaMemsetAsync(ctx->adj, 0, nvox * sizeof(float4), s));
     if (st != VR_OK) return st;
   }
+  // transfer-function gradient: per-block partial sums, reduced once after all views
+  const bool tf_partial = grad_tf && adjoint_tf_rows(ctx->ntf);
+  const int ablocks = adjoint_grid();
+  if (tf_partial) {
+    const size_t pbytes = (size_t)ablocks * 4 * ctx->ntf * sizeof(float);
+    void* pp = ctx->tf_partial;
+    st = ensure(ctx, &pp, &ctx->tf_partial_cap, pbytes);
+    if (st != VR_OK) return st;
+    ctx->tf_partial = static_cast<float*>(pp);
+    st = cuda_status(cudaMemsetAsync(ctx->tf_partial, 0, pbytes, s));
+    if (st != VR_OK) return st;
+  }
   // the adjoint visits every sample (no skipping): records are needed everywhere
   vr_render_params all = *params;
   all.skip_empty = 0;
@@ -598,7 +611,12 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
     L.grad_rgba = reinterpret_cast<const float4*>(grad_rgba[v]);
     L.adj = grad_volume ? ctx->adj : nullptr;
     L.grad_tf = grad_tf;
+    L.tf_partial = tf_partial ? ctx->tf_partial : nullptr;
     st = cuda_status(launch_adjoint(L, s));
+    if (st != VR_OK) return st;
+  }
+  if (tf_partial) {
+    st = cuda_status(launch_tf_partial_reduce(ctx->tf_partial, ablocks, 4 * ctx->ntf, grad_tf, s));
     if (st != VR_OK) return st;
   }
   if (grad_volume)

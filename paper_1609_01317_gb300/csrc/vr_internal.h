@@ -70,6 +70,9 @@ struct vr_ctx {
   // adjoint scratch: per voxel (dL/ds, dL/dG) at the cell corners, float4
   float4* adj = nullptr;
   size_t adj_cap = 0;
+  // per-block partial sums of the transfer-function gradient, [blocks][4 * ntf]
+  float* tf_partial = nullptr;
+  size_t tf_partial_cap = 0;
 
   // operator gradient records (G, V) per voxel and what they were computed for
   float4* rec = nullptr;
@@ -149,8 +152,19 @@ struct AdjointLaunch {
   const float4* grad_rgba;
   float4* adj;     // per voxel corner accumulators (dL/ds, dL/dG) over the unpadded grid
   float* grad_tf;  // n x 4, accumulated
+  // when non-null: [adjoint_grid()][4 n] per-block sums of the TF gradient, added to with
+  // vector reductions; grad_tf then receives them through launch_tf_partial_reduce instead
+  // of from the kernel
+  float* tf_partial;
 };
+// whether the TF gradient goes through per-block partial rows for a table of ntf entries,
+// and the persistent grid the adjoint launches
+bool adjoint_tf_rows(int ntf);
+int adjoint_grid();
 cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t s);
+// grad_tf[e] += sum over blocks b of partial[b][e], e < n4, in block order
+cudaError_t launch_tf_partial_reduce(const float* partial, int blocks, int n4, float* grad_tf,
+                                     cudaStream_t s);
 cudaError_t launch_adjoint_volume(const float4* adj, const int n[3], int op, float inv_vmax,
                                   float* grad_volume, cudaStream_t s);
 
