@@ -208,7 +208,7 @@ static vr_status refresh_visibility(vr_ctx* ctx, cudaStream_t s) {
   const float scale = (float)(ctx->ntf - 1) / ctx->value_max;
   return cuda_status(
       launch_brick_visibility(ctx->brick_minmax, ctx->nb, ctx->tf_prefix, ctx->ntf, scale,
-                              ctx->brick_vis, s));
+                              ctx->brick_vis, ctx->brick_list, s));
 }
 
 // Operator gradient records for the current volume, operator and (with skipping) the
@@ -224,7 +224,8 @@ vr_status ensure_records(vr_ctx* ctx, const vr_render_params* p, cudaStream_t s)
   if (st != VR_OK) return st;
   ctx->rec = static_cast<float4*>(r);
   st = cuda_status(launch_records(vol_dev(ctx), (int)ctx->dtype, p->grad,
-                                  skip ? ctx->brick_vis : nullptr, ctx->rec, s));
+                                  skip ? ctx->brick_vis : nullptr,
+                                  skip ? ctx->brick_list : nullptr, ctx->rec, s));
   if (st != VR_OK) {
     ctx->rec_valid = false;
     return st;
@@ -388,11 +389,14 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
                      (nz + kBrick - 1) / kBrick};
   const size_t nbricks = (size_t)nb[0] * nb[1] * nb[2];
   void* bt = ctx->brick_minmax;
-  st = ensure(ctx, &bt, &ctx->brick_cap, align256(nbricks * sizeof(float2)) + nbricks);
+  st = ensure(ctx, &bt, &ctx->brick_cap,
+              align256(nbricks * sizeof(float2)) + align256(nbricks) + (nbricks + 1) * sizeof(int));
   if (st != VR_OK) return st;
   ctx->brick_minmax = static_cast<float2*>(bt);
   ctx->brick_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) +
                                               align256(nbricks * sizeof(float2)));
+  ctx->brick_list = reinterpret_cast<int*>(static_cast<char*>(bt) +
+                                           align256(nbricks * sizeof(float2)) + align256(nbricks));
   ctx->dtype = dtype;
   ctx->n[0] = nx; ctx->n[1] = ny; ctx->n[2] = nz;
   ctx->px = (int)px; ctx->py = (int)py; ctx->pz = (int)pz;

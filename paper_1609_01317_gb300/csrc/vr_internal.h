@@ -42,6 +42,7 @@ struct vr_ctx {
   int nb[3] = {0, 0, 0};
   float2* brick_minmax = nullptr;
   uint8_t* brick_vis = nullptr;
+  int* brick_list = nullptr;  // [0]: count of visible bricks, then their indices
   size_t brick_cap = 0;
   void* upload_staging = nullptr;
   size_t upload_cap = 0;
@@ -114,11 +115,16 @@ cudaError_t launch_pad_volume(const void* src, int dtype, const int n[3], void* 
                               int py, int pz, cudaStream_t s);
 cudaError_t launch_brick_minmax(const VolDev& V, int dtype, float2* mm, cudaStream_t s);
 cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t s);
+// vis[b] for every brick; when `list` is non-null, list[0] must be zero and the visible
+// bricks' indices are appended after it (list[0] = their count, order unspecified)
 cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
-                                    int ntf, float scale, uint8_t* vis, cudaStream_t s);
+                                    int ntf, float scale, uint8_t* vis, int* list,
+                                    cudaStream_t s);
 
+// records of the bricks in `list` (as built by launch_brick_visibility, `need` its vis
+// array), or of every brick when `list` is null
 cudaError_t launch_records(const VolDev& V, int dtype, int op, const uint8_t* need,
-                           float4* rec, cudaStream_t s);
+                           const int* list, float4* rec, cudaStream_t s);
 
 struct MarchLaunch {
   VolDev V;

@@ -66,87 +66,107 @@ cudaError_t launch_pad_volume(const void* src, int dtype, const int n[3], void* 
 // ---------------------------------------------------------- brick min / max
 // Brick (bx, by, bz) covers voxels [8b, 8b+8) per axis.  Its footprint is
 // [8b - 1, 8b + 9] (clipped to the volume): every sample whose position lies within one
-// voxel of the brick box interpolates only voxels from it.  One warp per brick; each
-// lane reduces whole footprint rows, read as aligned vectors: in padded coordinates a
-// row of the footprint starts at x = 8 bx, a multiple of 8 elements, and the row pitch
-// is a multiple of 16 elements, so the loads below stay inside the padded row.
+// voxel of the brick box interpolates only voxels from it.
+//
+// One block per row of bricks (by, bz); its warps stream the padded rows of the row's
+// y / z footprint.  In padded coordinates (padded = voxel + 1) the x footprint of brick bx
+// is [8 bx, 8 bx + 10]; every padded element holds the clamp-to-edge value of a voxel
+// inside the clipped footprint or an edge voxel the clipped footprint contains, so the
+// x range needs no clipping.  Lane l takes the bricks 2l and 2l + 1 of a 64-brick segment:
+// one aligned 16-element vector (padded [16l', 16l' + 16), l' the brick pair) plus three
+// more elements for the second brick.  Rows in y and z are clipped to the volume.
 template <int VTYPE>
-__device__ __forceinline__ void row_minmax(const void* base, int lo, int hi, float& vmin,
-                                           float& vmax) {
-  float e[12];
+__device__ __forceinline__ void load16(const typename VoxelT<VTYPE>::T* p, float e[16]) {
   if constexpr (VTYPE == VT_U8) {
-    const uint2 a = *reinterpret_cast<const uint2*>(base);
-    const uint2 b = hi >= 8 ? *(reinterpret_cast<const uint2*>(base) + 1) : make_uint2(0, 0);
-    const unsigned w[4] = {a.x, a.y, b.x, b.y};
+    const uint4 a = *reinterpret_cast<const uint4*>(p);
+    const unsigned w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-    for (int j = 0; j < 12; ++j) e[j] = (float)((w[j >> 2] >> (8 * (j & 3))) & 0xffu);
+    for (int j = 0; j < 16; ++j) e[j] = (float)((w[j >> 2] >> (8 * (j & 3))) & 0xffu);
   } else if constexpr (VTYPE == VT_U16 || VTYPE == VT_F16) {
-    const uint4 a = *reinterpret_cast<const uint4*>(base);
-    const uint4 b = hi >= 8 ? *(reinterpret_cast<const uint4*>(base) + 1) : make_uint4(0, 0, 0, 0);
-    const unsigned w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+    const uint4 a = *reinterpret_cast<const uint4*>(p);
+    const uint4 b = *(reinterpret_cast<const uint4*>(p) + 1);
+    const unsigned w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
+    for (int j = 0; j < 16; ++j) {
       const unsigned short h = (unsigned short)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
       if constexpr (VTYPE == VT_U16) e[j] = (float)h;
       else e[j] = __half2float(__ushort_as_half(h));
     }
   } else {
-    const float4 a = *reinterpret_cast<const float4*>(base);
-    const float4 b = *(reinterpret_cast<const float4*>(base) + 1);
-    const float4 c = hi >= 8 ? *(reinterpret_cast<const float4*>(base) + 2) : make_float4(0, 0, 0, 0);
-    const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 #pragma unroll
-    for (int j = 0; j < 12; ++j) e[j] = w[j];
-  }
-#pragma unroll
-  for (int j = 0; j < 11; ++j) {
-    if (j >= lo && j <= hi) {
-      vmin = fminf(vmin, e[j]);
-      vmax = fmaxf(vmax, e[j]);
+    for (int k = 0; k < 4; ++k) {
+      const float4 a = *(reinterpret_cast<const float4*>(p) + k);
+      e[4 * k] = a.x; e[4 * k + 1] = a.y; e[4 * k + 2] = a.z; e[4 * k + 3] = a.w;
     }
   }
 }
 
+constexpr int kMinmaxWarps = 8;
+
 template <int VTYPE>
-__global__ void k_brick_minmax(const VolDev V, float2* __restrict__ mm, int nbricks) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= nbricks) return;
-  const int bx = warp % V.nb[0];
-  const int by = (warp / V.nb[0]) % V.nb[1];
-  const int bz = warp / (V.nb[0] * V.nb[1]);
-  // footprint in padded coordinates (padded = voxel + 1)
-  const int x0 = bx << kBrickShift;  // padded x of voxel 8bx - 1
-  const int xlo = max((bx << kBrickShift) - 1, 0) + kPadLo - x0;
-  const int xhi = min((bx << kBrickShift) + kBrick + 1, V.n[0] - 1) + kPadLo - x0;
+__global__ void __launch_bounds__(32 * kMinmaxWarps) k_brick_minmax(const VolDev V, float2* __restrict__ mm) {
+  __shared__ float2 red[kMinmaxWarps][64];
+  const int by = blockIdx.x, bz = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nbx = V.nb[0];
   const int ylo = max((by << kBrickShift) - 1, 0), yhi = min((by << kBrickShift) + kBrick + 1, V.n[1] - 1);
   const int zlo = max((bz << kBrickShift) - 1, 0), zhi = min((bz << kBrickShift) + kBrick + 1, V.n[2] - 1);
   const int ey = yhi - ylo + 1, nrows = ey * (zhi - zlo + 1);
-  constexpr int esize = (VTYPE == VT_U8) ? 1 : ((VTYPE == VT_F32) ? 4 : 2);
-  const char* data = static_cast<const char*>(V.data);
-  float vmin = __int_as_float(0x7f800000), vmax = -vmin;
-  for (int r = lane; r < nrows; r += 32) {
-    const int y = ylo + r % ey, z = zlo + r / ey;
-    const size_t off = (size_t)x0 + (size_t)V.px * (y + kPadLo) + (size_t)V.pxy * (z + kPadLo);
-    row_minmax<VTYPE>(data + off * esize, xlo, xhi, vmin, vmax);
-  }
+  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
+  const float inf = __int_as_float(0x7f800000);
+  for (int seg = 0; seg < nbx; seg += 64) {
+    const int b0 = seg + 2 * lane;
+    const bool has0 = b0 < nbx, has1 = b0 + 1 < nbx;
+    float mn0 = inf, mx0 = -inf, mn1 = inf, mx1 = -inf;
+    for (int r = warp; r < nrows && has0; r += kMinmaxWarps) {
+      const int y = ylo + r % ey, z = zlo + r / ey;
+      const auto* row = v + (size_t)V.px * (y + kPadLo) + (size_t)V.pxy * (z + kPadLo);
+      float e[16];
+      load16<VTYPE>(row + (b0 << kBrickShift), e);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      for (int j = 0; j <= 10; ++j) {
+        mn0 = fminf(mn0, e[j]);
+        mx0 = fmaxf(mx0, e[j]);
+      }
+      if (has1) {
+#pragma unroll
+        for (int j = 8; j < 16; ++j) {
+          mn1 = fminf(mn1, e[j]);
+          mx1 = fmaxf(mx1, e[j]);
+        }
+#pragma unroll
+        for (int j = 16; j <= 18; ++j) {
+          const float x = ldv<VTYPE>(row, (b0 << kBrickShift) + j);
+          mn1 = fminf(mn1, x);
+          mx1 = fmaxf(mx1, x);
+        }
+      }
+    }
+    red[warp][2 * lane] = make_float2(mn0, mx0);
+    red[warp][2 * lane + 1] = make_float2(mn1, mx1);
+    __syncthreads();
+    if (threadIdx.x < 64 && seg + (int)threadIdx.x < nbx) {
+      float2 m = red[0][threadIdx.x];
+#pragma unroll
+      for (int w = 1; w < kMinmaxWarps; ++w) {
+        const float2 o = red[w][threadIdx.x];
+        m.x = fminf(m.x, o.x);
+        m.y = fmaxf(m.y, o.y);
+      }
+      mm[(size_t)(bz * V.nb[1] + by) * nbx + seg + threadIdx.x] = m;
+    }
+    __syncthreads();
   }
-  if (lane == 0) mm[warp] = make_float2(vmin, vmax);
 }
 
 cudaError_t launch_brick_minmax(const VolDev& V, int dtype, float2* mm, cudaStream_t s) {
-  const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
-  const int threads = 256;
-  const int blocks = (nbricks * 32 + threads - 1) / threads;
+  const dim3 grid(V.nb[1], V.nb[2]);
+  const int threads = 32 * kMinmaxWarps;
   switch (dtype) {
-    case VT_U8: k_brick_minmax<VT_U8><<<blocks, threads, 0, s>>>(V, mm, nbricks); break;
-    case VT_U16: k_brick_minmax<VT_U16><<<blocks, threads, 0, s>>>(V, mm, nbricks); break;
-    case VT_F16: k_brick_minmax<VT_F16><<<blocks, threads, 0, s>>>(V, mm, nbricks); break;
-    default: k_brick_minmax<VT_F32><<<blocks, threads, 0, s>>>(V, mm, nbricks);
+    case VT_U8: k_brick_minmax<VT_U8><<<grid, threads, 0, s>>>(V, mm); break;
+    case VT_U16: k_brick_minmax<VT_U16><<<grid, threads, 0, s>>>(V, mm); break;
+    case VT_F16: k_brick_minmax<VT_F16><<<grid, threads, 0, s>>>(V, mm); break;
+    default: k_brick_minmax<VT_F32><<<grid, threads, 0, s>>>(V, mm);
   }
   return cudaGetLastError();
 }
@@ -189,24 +209,41 @@ cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t 
 // excursion of an interpolated value cannot reach an unchecked entry.
 __global__ void k_brick_visibility(const float2* __restrict__ mm, int nbricks,
                                    const int* __restrict__ prefix, int ntf, float scale,
-                                   uint8_t* __restrict__ vis) {
+                                   uint8_t* __restrict__ vis, int* __restrict__ list) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nbricks) return;
-  const float2 m = mm[i];
-  const float top = (float)(ntf - 1);
-  const float ulo = fminf(fmaxf(m.x * scale, 0.0f), top);
-  const float uhi = fminf(fmaxf(m.y * scale, 0.0f), top);
-  const int jlo = max((int)ulo - 1, 0);
-  const int jhi = min((int)uhi + 2, ntf - 1);
-  vis[i] = (prefix[jhi + 1] - prefix[jlo]) > 0 ? 1 : 0;
+  bool visible = false;
+  if (i < nbricks) {
+    const float2 m = mm[i];
+    const float top = (float)(ntf - 1);
+    const float ulo = fminf(fmaxf(m.x * scale, 0.0f), top);
+    const float uhi = fminf(fmaxf(m.y * scale, 0.0f), top);
+    const int jlo = max((int)ulo - 1, 0);
+    const int jhi = min((int)uhi + 2, ntf - 1);
+    visible = (prefix[jhi + 1] - prefix[jlo]) > 0;
+    vis[i] = visible ? 1 : 0;
+  }
+  if (list) {
+    // one atomic per warp for its visible bricks
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, visible);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(list, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (visible) list[1 + base + __popc(m & ((1u << lane) - 1u))] = i;
+  }
 }
 
 cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
-                                    int ntf, float scale, uint8_t* vis, cudaStream_t s) {
+                                    int ntf, float scale, uint8_t* vis, int* list,
+                                    cudaStream_t s) {
   const int nbricks = nb[0] * nb[1] * nb[2];
   const int threads = 256;
+  if (list) {
+    const cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   k_brick_visibility<<<(nbricks + threads - 1) / threads, threads, 0, s>>>(mm, nbricks, prefix,
-                                                                          ntf, scale, vis);
+                                                                          ntf, scale, vis, list);
   return cudaGetLastError();
 }
 
@@ -223,106 +260,140 @@ namespace vr {
 // march reads 8 records per sample instead of evaluating the taps.
 //
 // A brick needs the records of voxels [8b, 8b+8]^3 (its cells' corners); with skipping
-// on, only visible bricks are visited.  One block per brick: the 11^3 clamp-to-edge
-// neighbourhood [8b-1, 8b+9]^3 is staged in shared memory, then each thread computes
-// records from it.
+// on, only visible bricks are visited.  Each voxel is written by the brick whose core
+// [8b, 8b+8)^3 holds it when that brick is computed, else by the computed brick whose
+// upper face it lies on (several such bricks write the same value).  Persistent blocks take
+// bricks in grid stride: the 11^3 clamp-to-edge neighbourhood [8b-1, 8b+9]^3 is staged in
+// shared memory, then 81 threads each stream one (x, y) column of records along z.
 template <int VTYPE, int OP>
 __global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* __restrict__ need,
+                                                 const int* __restrict__ list,
                                                  float4* __restrict__ rec) {
   __shared__ float tile[11][11][12];  // [z][y][x], x padded to 12
-  const int bid = blockIdx.x;
-  if (need && !need[bid]) return;
   const int t = threadIdx.x;
-  const int bx = bid % V.nb[0], by = (bid / V.nb[0]) % V.nb[1], bz = bid / (V.nb[0] * V.nb[1]);
-  const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
+  const int nbx = V.nb[0], nby = V.nb[1];
+  const int nbricks = nbx * nby * V.nb[2];
   const int nx = V.n[0], ny = V.n[1], nz = V.n[2];
   const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
-  // stage: thread (i, j) loads the z column of [x0-1+i, y0-1+j]; coordinates beyond n
-  // are clamped to n (still inside the padded border, where E is the edge value)
-  if (t < 121) {
-    const int i = t % 11, j = t / 11;
-    const int X = min(x0 - 1 + i, nx), Y = min(y0 - 1 + j, ny);
-    const int colp = (X + kPadLo) + V.px * (Y + kPadLo);
+  const int u = t % 9, w = t / 9;  // x, y offsets in the brick (threads below 81)
+  const int nwork = list ? list[0] : nbricks;
+  for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
+    const int bid = list ? list[1 + item] : item;
+    const int bx = bid % nbx, by = (bid / nbx) % nby, bz = bid / (nbx * nby);
+    const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
+    // stage: thread (i, j) loads the z column of [x0-1+i, y0-1+j]; coordinates beyond n
+    // are clamped to n (still inside the padded border, where E is the edge value)
+    if (t < 121) {
+      const int i = t % 11, j = t / 11;
+      const int X = min(x0 - 1 + i, nx), Y = min(y0 - 1 + j, ny);
+      const int colp = (X + kPadLo) + V.px * (Y + kPadLo);
 #pragma unroll
-    for (int k = 0; k < 11; ++k) {
-      const int Z = min(z0 - 1 + k, nz);
-      tile[k][j][i] = ldv<VTYPE>(v, colp + V.pxy * (Z + kPadLo));
+      for (int k = 0; k < 11; ++k) {
+        const int Z = min(z0 - 1 + k, nz);
+        tile[k][j][i] = ldv<VTYPE>(v, colp + V.pxy * (Z + kPadLo));
+      }
     }
-  }
-  __syncthreads();
-  if (t >= 81) return;
-  const int u = t % 9, w = t / 9;  // x, y offsets in the brick
-  const int x = x0 + u, y = y0 + w;
-  if (x >= nx || y >= ny) return;
-  constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
-  constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
-  constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
-  float P[3][3][3];  // [z][y][x] neighbourhood of the current voxel, rolled along z
+    __syncthreads();
+    const int x = x0 + u, y = y0 + w;
+    if (t < 81 && x < nx && y < ny) {
+      // which of this column's records to write: the core always; a face voxel when the
+      // brick that owns it is not computed
+      const int ox = u == kBrick, oy = w == kBrick;
+      bool wr_lo = true, wr_top = false;
+      if (need) {
+        if (ox | oy) wr_lo = !need[(bx + ox) + nbx * ((by + oy) + nby * bz)];
+        if (z0 + kBrick < nz) wr_top = !need[(bx + ox) + nbx * ((by + oy) + nby * (bz + 1))];
+      } else {
+        wr_lo = !(ox | oy);
+      }
+      constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+      constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+      constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+      float P[3][3][3];  // [z][y][x] neighbourhood of the current voxel, rolled along z
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+      for (int c = 0; c < 2; ++c)
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+        for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) P[c][b][a] = tile[c][w + b][u + a];
-  const int qn = min(kBrick + 1, nz - z0);
-  float4* out = rec + (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z0);
-  const size_t zstride = (size_t)nx * ny;
-  for (int q = 0; q < qn; ++q) {
+          for (int a = 0; a < 3; ++a) P[c][b][a] = tile[c][w + b][u + a];
+      const int qn = min(kBrick + 1, nz - z0);
+      float4* out = rec + (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z0);
+      const size_t zstride = (size_t)nx * ny;
+      for (int q = 0; q < qn; ++q) {
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+        for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) P[2][b][a] = tile[q + 2][w + b][u + a];
-    float g[3];
-    if constexpr (OP == OP_CENTRAL) {
-      g[0] = P[1][1][2] - P[1][1][0];
-      g[1] = P[1][2][1] - P[1][0][1];
-      g[2] = P[2][1][1] - P[0][1][1];
-    } else {
-      float d[3][3][3];  // difference planes along x ([z][y]), y ([z][x]), z ([y][x])
+          for (int a = 0; a < 3; ++a) P[2][b][a] = tile[q + 2][w + b][u + a];
+        if (q < kBrick ? wr_lo : wr_top) {
+          float g[3];
+          if constexpr (OP == OP_CENTRAL) {
+            g[0] = P[1][1][2] - P[1][1][0];
+            g[1] = P[1][2][1] - P[1][0][1];
+            g[2] = P[2][1][1] - P[0][1][1];
+          } else {
+            float d[3][3][3];  // difference planes along x ([z][y]), y ([z][x]), z ([y][x])
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
+            for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          d[0][a][b] = P[a][b][2] - P[a][b][0];
-          d[1][a][b] = P[a][2][b] - P[a][0][b];
-          d[2][a][b] = P[2][a][b] - P[0][a][b];
+              for (int b = 0; b < 3; ++b) {
+                d[0][a][b] = P[a][b][2] - P[a][b][0];
+                d[1][a][b] = P[a][2][b] - P[a][0][b];
+                d[2][a][b] = P[2][a][b] - P[0][a][b];
+              }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float edges = (d[c][0][1] + d[c][2][1]) + (d[c][1][0] + d[c][1][2]);
+              const float corners = (d[c][0][0] + d[c][0][2]) + (d[c][2][0] + d[c][2][2]);
+              g[c] = fmaf(w0, d[c][1][1], fmaf(w1, edges, w2 * corners));
+            }
+          }
+          out[q * zstride] = make_float4(g[0], g[1], g[2], P[1][1][1]);
         }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float edges = (d[c][0][1] + d[c][2][1]) + (d[c][1][0] + d[c][1][2]);
-        const float corners = (d[c][0][0] + d[c][0][2]) + (d[c][2][0] + d[c][2][2]);
-        g[c] = fmaf(w0, d[c][1][1], fmaf(w1, edges, w2 * corners));
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            P[0][b][a] = P[1][b][a];
+            P[1][b][a] = P[2][b][a];
+          }
       }
     }
-    out[q * zstride] = make_float4(g[0], g[1], g[2], P[1][1][1]);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        P[0][b][a] = P[1][b][a];
-        P[1][b][a] = P[2][b][a];
-      }
+    __syncthreads();  // the tile is restaged for the next brick
   }
 }
 
-template <int VTYPE>
-static void launch_records_op(const VolDev& V, int op, const uint8_t* need, float4* rec,
-                              cudaStream_t s) {
+template <int VTYPE, int OP>
+static void launch_records_k(const VolDev& V, const uint8_t* need, const int* list, float4* rec,
+                             cudaStream_t s) {
+  static int grid = 0;  // persistent grid: SMs x resident blocks (same device for a process)
+  if (grid == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_records<VTYPE, OP>, 128, 0);
+    grid = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+  }
   const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
+  k_records<VTYPE, OP><<<min(grid, nbricks), 128, 0, s>>>(V, need, list, rec);
+}
+
+template <int VTYPE>
+static void launch_records_op(const VolDev& V, int op, const uint8_t* need, const int* list,
+                              float4* rec, cudaStream_t s) {
   switch (op) {
-    case OP_CENTRAL: k_records<VTYPE, OP_CENTRAL><<<nbricks, 128, 0, s>>>(V, need, rec); break;
-    case OP_SOBEL: k_records<VTYPE, OP_SOBEL><<<nbricks, 128, 0, s>>>(V, need, rec); break;
-    default: k_records<VTYPE, OP_ZH><<<nbricks, 128, 0, s>>>(V, need, rec);
+    case OP_CENTRAL: launch_records_k<VTYPE, OP_CENTRAL>(V, need, list, rec, s); break;
+    case OP_SOBEL: launch_records_k<VTYPE, OP_SOBEL>(V, need, list, rec, s); break;
+    default: launch_records_k<VTYPE, OP_ZH>(V, need, list, rec, s);
   }
 }
 
 cudaError_t launch_records(const VolDev& V, int dtype, int op, const uint8_t* need,
-                           float4* rec, cudaStream_t s) {
+                           const int* list, float4* rec, cudaStream_t s) {
   switch (dtype) {
-    case VT_U8: launch_records_op<VT_U8>(V, op, need, rec, s); break;
-    case VT_U16: launch_records_op<VT_U16>(V, op, need, rec, s); break;
-    case VT_F16: launch_records_op<VT_F16>(V, op, need, rec, s); break;
-    default: launch_records_op<VT_F32>(V, op, need, rec, s);
+    case VT_U8: launch_records_op<VT_U8>(V, op, need, list, rec, s); break;
+    case VT_U16: launch_records_op<VT_U16>(V, op, need, list, rec, s); break;
+    case VT_F16: launch_records_op<VT_F16>(V, op, need, list, rec, s); break;
+    default: launch_records_op<VT_F32>(V, op, need, list, rec, s);
   }
   return cudaGetLastError();
 }
