@@ -102,6 +102,8 @@ VolDev vol_dev(const vr_ctx* ctx) {
   V.pxy = ctx->px * ctx->py;
   V.value_max = ctx->value_max;
   V.vis = ctx->brick_vis;
+  V.mvis = ctx->macro_vis;
+  for (int a = 0; a < 3; ++a) V.nm[a] = ctx->nm[a];
   return V;
 }
 
@@ -208,7 +210,7 @@ static vr_status refresh_visibility(vr_ctx* ctx, cudaStream_t s) {
   const float scale = (float)(ctx->ntf - 1) / ctx->value_max;
   return cuda_status(
       launch_brick_visibility(ctx->brick_minmax, ctx->nb, ctx->tf_prefix, ctx->ntf, scale,
-                              ctx->brick_vis, ctx->brick_list, s));
+                              ctx->brick_vis, ctx->brick_list, ctx->macro_vis, ctx->nm, s));
 }
 
 // Operator gradient records for the current volume, operator and (with skipping) the
@@ -389,18 +391,25 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
                      (nz + kBrick - 1) / kBrick};
   const size_t nbricks = (size_t)nb[0] * nb[1] * nb[2];
   void* bt = ctx->brick_minmax;
-  st = ensure(ctx, &bt, &ctx->brick_cap,
-              align256(nbricks * sizeof(float2)) + align256(nbricks) + (nbricks + 1) * sizeof(int));
+  const int nm[3] = {(nb[0] + 3) >> kMacroShift, (nb[1] + 3) >> kMacroShift,
+                     (nb[2] + 3) >> kMacroShift};
+  const size_t nmacro = (size_t)nm[0] * nm[1] * nm[2];
+  const size_t off_vis = align256(nbricks * sizeof(float2));
+  const size_t off_list = off_vis + align256(nbricks);
+  const size_t off_macro = off_list + align256((nbricks + 1) * sizeof(int));
+  st = ensure(ctx, &bt, &ctx->brick_cap, off_macro + nmacro);
   if (st != VR_OK) return st;
   ctx->brick_minmax = static_cast<float2*>(bt);
-  ctx->brick_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) +
-                                              align256(nbricks * sizeof(float2)));
-  ctx->brick_list = reinterpret_cast<int*>(static_cast<char*>(bt) +
-                                           align256(nbricks * sizeof(float2)) + align256(nbricks));
+  ctx->brick_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) + off_vis);
+  ctx->brick_list = reinterpret_cast<int*>(static_cast<char*>(bt) + off_list);
+  ctx->macro_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) + off_macro);
   ctx->dtype = dtype;
   ctx->n[0] = nx; ctx->n[1] = ny; ctx->n[2] = nz;
   ctx->px = (int)px; ctx->py = (int)py; ctx->pz = (int)pz;
-  for (int a = 0; a < 3; ++a) ctx->nb[a] = nb[a];
+  for (int a = 0; a < 3; ++a) {
+    ctx->nb[a] = nb[a];
+    ctx->nm[a] = nm[a];
+  }
   ctx->value_max = value_max;
   st = cuda_status(launch_pad_volume(src, (int)dtype, ctx->n, ctx->vol, ctx->px, ctx->py,
                                      ctx->pz, s));
@@ -410,6 +419,8 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
   if (!ctx->has_tf) {
     // no transfer function yet: everything visible until one is set
     st = cuda_status(cudaMemsetAsync(ctx->brick_vis, 1, nbricks, s));
+    if (st != VR_OK) return st;
+    st = cuda_status(cudaMemsetAsync(ctx->macro_vis, 1, nmacro, s));
     if (st != VR_OK) return st;
   }
   ctx->has_volume = true;

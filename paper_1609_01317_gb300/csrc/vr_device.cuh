@@ -14,6 +14,7 @@ namespace vr {
 
 constexpr int kBrick = 8;       // brick edge in voxels (empty-space skipping, §5.3)
 constexpr int kBrickShift = 3;
+constexpr int kMacroShift = 2;  // a macro brick is 4 x 4 x 4 bricks (32^3 voxels)
 constexpr int kCkptStride = 32; // samples per adjoint checkpoint segment
 constexpr int kPadLo = 1;       // clamp-to-edge border below each axis
 constexpr int kPadHi = 2;       // ... and above (covers the 4^3 stencil of the last cell)
@@ -38,6 +39,8 @@ struct VolDev {
   float value_max;   // raw -> [0,1]
   int nb[3];         // bricks per axis
   const uint8_t* vis;  // per-brick visibility (1 = some sample may be non-transparent)
+  const uint8_t* mvis;  // per-macro-brick visibility (OR over its bricks), or null
+  int nm[3];            // macro bricks per axis
 };
 
 // Gradient records over the unpadded grid: rec[x + nx*(y + ny*z)] = (G_x, G_y, G_z, V).
@@ -76,6 +79,15 @@ template <> struct VoxelT<VT_U8> { using T = uint8_t; };
 template <> struct VoxelT<VT_U16> { using T = uint16_t; };
 template <> struct VoxelT<VT_F16> { using T = __half; };
 template <> struct VoxelT<VT_F32> { using T = float; };
+
+template <int VTYPE>
+__device__ __forceinline__ float to_float(typename VoxelT<VTYPE>::T x) {
+  if constexpr (VTYPE == VT_F16) {
+    return __half2float(x);
+  } else {
+    return static_cast<float>(x);
+  }
+}
 
 template <int VTYPE>
 __device__ __forceinline__ float ldv(const typename VoxelT<VTYPE>::T* __restrict__ v, int off) {
@@ -412,6 +424,23 @@ __device__ __forceinline__ int brick_of(const VolDev& V, const float p[3], int b
     b[a] = i < 0 ? 0 : (i >= V.nb[a] ? V.nb[a] - 1 : i);
   }
   return b[0] + V.nb[0] * (b[1] + V.nb[1] * b[2]);
+}
+
+// First sample index whose t lies at or beyond the exit of the axis-aligned region
+// [c << shift, (c + 1) << shift) (a brick for shift 3, a macro brick for shift 5), with the
+// ray's reciprocal direction and step precomputed.  Rounding of t is harmless: every brick's
+// footprint covers one voxel around it, so samples just past the exit are still transparent.
+__device__ __forceinline__ int region_exit_sample(const int c[3], int shift, const float o[3],
+                                                  const float d[3], const float inv_d[3],
+                                                  float tn, float inv_step) {
+  float te = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] > 0.0f) te = fminf(te, ((float)((c[a] + 1) << shift) - o[a]) * inv_d[a]);
+    else if (d[a] < 0.0f) te = fminf(te, ((float)(c[a] << shift) - o[a]) * inv_d[a]);
+  }
+  const float kf = ceilf(fmaf(te - tn, inv_step, -0.5f));
+  return kf > 2.0e9f ? 2000000000 : (int)kf;
 }
 
 // First sample index whose t lies at or beyond the exit of brick b (§5.3 skipping; the

@@ -43,6 +43,8 @@ struct vr_ctx {
   float2* brick_minmax = nullptr;
   uint8_t* brick_vis = nullptr;
   int* brick_list = nullptr;  // [0]: count of visible bricks, then their indices
+  uint8_t* macro_vis = nullptr;  // per macro brick (4^3 bricks): OR of the bricks' visibility
+  int nm[3] = {0, 0, 0};
   size_t brick_cap = 0;
   void* upload_staging = nullptr;
   size_t upload_cap = 0;
@@ -115,12 +117,12 @@ cudaError_t launch_pad_volume(const void* src, int dtype, const int n[3], void* 
                               int py, int pz, cudaStream_t s);
 cudaError_t launch_brick_minmax(const VolDev& V, int dtype, float2* mm, cudaStream_t s);
 cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t s);
-// vis[b] for every brick; when `list` is non-null, list[0] must be zero and the visible
-// bricks' indices are appended after it (list[0] = their count, order unspecified)
+// vis[b] for every brick; when `list` is non-null, its visible bricks' indices are written
+// after list[0] (= their count, order unspecified); when `mvis` is non-null, mvis[m] = OR of
+// vis over the bricks of macro brick m (grid nm)
 cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
                                     int ntf, float scale, uint8_t* vis, int* list,
-                                    cudaStream_t s);
-
+                                    uint8_t* mvis, const int nm[3], cudaStream_t s);
 // records of the bricks in `list` (as built by launch_brick_visibility, `need` its vis
 // array), or of every brick when `list` is null
 cudaError_t launch_records(const VolDev& V, int dtype, int op, const uint8_t* need,

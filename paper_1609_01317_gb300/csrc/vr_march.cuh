@@ -69,6 +69,10 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
   float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
   int k = 0;
   const float step = L.r.step;
+  const float inv_step = 1.0f / step;
+  float inv_d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) inv_d[a] = d[a] != 0.0f ? 1.0f / d[a] : 0.0f;
   while (k < K) {
     const int ks = k + q;
     const bool live = ks < K;
@@ -82,8 +86,19 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
       int b[3];
       const int bi = brick_of(L.V, p, b);
       if (!__ldg(L.V.vis + bi)) {
+        // transparent brick: leave it, or its whole macro brick when that is transparent too
         vis = false;
-        kn = brick_exit_sample(b, o, d, tn, step);
+        int shift = kBrickShift;
+        if (L.V.mvis) {
+          const int m[3] = {b[0] >> kMacroShift, b[1] >> kMacroShift, b[2] >> kMacroShift};
+          if (!__ldg(L.V.mvis + m[0] + L.V.nm[0] * (m[1] + L.V.nm[1] * m[2]))) {
+            b[0] = m[0];
+            b[1] = m[1];
+            b[2] = m[2];
+            shift = kBrickShift + kMacroShift;
+          }
+        }
+        kn = region_exit_sample(b, shift, o, d, inv_d, tn, inv_step);
         if (kn <= ks) kn = ks + 1;
       }
     }

@@ -260,7 +260,7 @@ extern "C" vr_status vr_render_noalloc(const void* voxels, vr_dtype dtype, int n
   st = cuda_status(launch_tf_prefix(tf, ntf, prefix, s));
   if (st != VR_OK) return st;
   const float scale = (float)(ntf - 1) / value_max;
-  st = cuda_status(launch_brick_visibility(mm, nb, prefix, ntf, scale, vis, nullptr, s));
+  st = cuda_status(launch_brick_visibility(mm, nb, prefix, ntf, scale, vis, nullptr, nullptr, nullptr, s));
   if (st != VR_OK) return st;
   st = cuda_status(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
   if (st != VR_OK) return st;
@@ -275,6 +275,8 @@ extern "C" vr_status vr_render_noalloc(const void* voxels, vr_dtype dtype, int n
   L.V.px = L.V.py = L.V.pxy = 0;
   L.V.value_max = value_max;
   L.V.vis = vis;
+  L.V.mvis = nullptr;
+  L.V.nm[0] = L.V.nm[1] = L.V.nm[2] = 0;
   L.tf.tf = tf;
   L.tf.n = ntf;
   L.tf.scale = scale;

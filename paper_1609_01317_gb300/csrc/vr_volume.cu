@@ -204,12 +204,16 @@ cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t 
 
 // ------------------------------------------------------------ brick visibility
 // A brick is invisible when every table entry a sample in it can touch has alpha == 0.
+// A macro brick (4 x 4 x 4 bricks) is visible when any of its bricks is: a ray may leave a
+// transparent macro brick at its exit in one step (the bricks' footprints, and so their
+// union, extend one voxel beyond it).
 // The table coordinate is computed with the same FP32 expression as the march
 // (u = raw * scale, clamped), widened by one entry below and two above so that a one-ulp
 // excursion of an interpolated value cannot reach an unchecked entry.
-__global__ void k_brick_visibility(const float2* __restrict__ mm, int nbricks,
+__global__ void k_brick_visibility(const float2* __restrict__ mm, int nbx, int nby, int nbricks,
                                    const int* __restrict__ prefix, int ntf, float scale,
-                                   uint8_t* __restrict__ vis, int* __restrict__ list) {
+                                   uint8_t* __restrict__ vis, int* __restrict__ list,
+                                   uint8_t* __restrict__ mvis, int nmx, int nmy) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool visible = false;
   if (i < nbricks) {
@@ -221,6 +225,11 @@ __global__ void k_brick_visibility(const float2* __restrict__ mm, int nbricks,
     const int jhi = min((int)uhi + 2, ntf - 1);
     visible = (prefix[jhi + 1] - prefix[jlo]) > 0;
     vis[i] = visible ? 1 : 0;
+    if (visible && mvis) {
+      // the macro brick holding this brick is visible (every writer stores the same 1)
+      const int bx = i % nbx, by = (i / nbx) % nby, bz = i / (nbx * nby);
+      mvis[(bx >> kMacroShift) + nmx * ((by >> kMacroShift) + nmy * (bz >> kMacroShift))] = 1;
+    }
   }
   if (list) {
     // one atomic per warp for its visible bricks
@@ -235,15 +244,20 @@ __global__ void k_brick_visibility(const float2* __restrict__ mm, int nbricks,
 
 cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
                                     int ntf, float scale, uint8_t* vis, int* list,
-                                    cudaStream_t s) {
+                                    uint8_t* mvis, const int nm[3], cudaStream_t s) {
   const int nbricks = nb[0] * nb[1] * nb[2];
   const int threads = 256;
   if (list) {
     const cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
   }
-  k_brick_visibility<<<(nbricks + threads - 1) / threads, threads, 0, s>>>(mm, nbricks, prefix,
-                                                                          ntf, scale, vis, list);
+  if (mvis) {
+    const cudaError_t e = cudaMemsetAsync(mvis, 0, (size_t)nm[0] * nm[1] * nm[2], s);
+    if (e != cudaSuccess) return e;
+  }
+  k_brick_visibility<<<(nbricks + threads - 1) / threads, threads, 0, s>>>(
+      mm, nb[0], nb[1], nbricks, prefix, ntf, scale, vis, list, mvis, mvis ? nm[0] : 0,
+      mvis ? nm[1] : 0);
   return cudaGetLastError();
 }
 
@@ -265,6 +279,46 @@ namespace vr {
 // upper face it lies on (several such bricks write the same value).  Persistent blocks take
 // bricks in grid stride: the 11^3 clamp-to-edge neighbourhood [8b-1, 8b+9]^3 is staged in
 // shared memory, then 81 threads each stream one (x, y) column of records along z.
+// Sums of one z plane of a voxel's 3x3x3 neighbourhood (pl[y][x], the voxel at [w+1][u+1])
+// from which the operators of §3.5 are assembled.  Every 3x3x3 operator here weights a tap
+// by its class only: centre w0, edge w1, corner w2 of the 3x3 mask across the component's
+// axis.  With d_x(b) the difference along x in row b of the plane, and likewise d_y(a):
+//   ax = d_x(0), bx = d_x(-1) + d_x(+1), ay = d_y(0), by = d_y(-1) + d_y(+1),
+//   q  = the plane weighted by the mask (for the z component), c = the voxel's own value.
+// G_x = w0 ax(z) + w1 (bx(z) + ax(z-1) + ax(z+1)) + w2 (bx(z-1) + bx(z+1)), G_y likewise,
+// G_z = q(z+1) - q(z-1); central differences use ax, ay and c only.
+struct PlaneSums {
+  float ax, bx, ay, by, q, c;
+};
+
+template <int OP>
+__device__ __forceinline__ PlaneSums plane_sums(const float (*pl)[12], int u, int w) {
+  PlaneSums r;
+  if constexpr (OP == OP_CENTRAL) {
+    r.ax = pl[w + 1][u + 2] - pl[w + 1][u];
+    r.ay = pl[w + 2][u + 1] - pl[w][u + 1];
+    r.c = pl[w + 1][u + 1];
+    r.bx = r.by = r.q = 0.0f;
+  } else {
+    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+    float p[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) p[b][a] = pl[w + b][u + a];
+    r.ax = p[1][2] - p[1][0];
+    r.bx = (p[0][2] - p[0][0]) + (p[2][2] - p[2][0]);
+    r.ay = p[2][1] - p[0][1];
+    r.by = (p[2][0] - p[0][0]) + (p[2][2] - p[0][2]);
+    r.q = fmaf(w0, p[1][1], fmaf(w1, (p[0][1] + p[2][1]) + (p[1][0] + p[1][2]),
+                                 w2 * ((p[0][0] + p[0][2]) + (p[2][0] + p[2][2]))));
+    r.c = p[1][1];
+  }
+  return r;
+}
+
 template <int VTYPE, int OP>
 __global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* __restrict__ need,
                                                  const int* __restrict__ list,
@@ -277,21 +331,31 @@ __global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* 
   const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
   const int u = t % 9, w = t / 9;  // x, y offsets in the brick (threads below 81)
   const int nwork = list ? list[0] : nbricks;
+  using T = typename VoxelT<VTYPE>::T;
+  // stage: thread (i, j) < 121 loads the z column of [x0-1+i, y0-1+j] of a brick;
+  // coordinates beyond n are clamped to n (still inside the padded border, where E is the
+  // edge value).  The next brick's columns are loaded into registers while the current one
+  // is computed.
+  const int si = t % 11, sj = t / 11;
+  T col[11];
+  auto load_columns = [&](int item) {
+    const int b = list ? list[1 + item] : item;
+    const int X = min(((b % nbx) << kBrickShift) - 1 + si, nx);
+    const int Y = min((((b / nbx) % nby) << kBrickShift) - 1 + sj, ny);
+    const int Z0 = (b / (nbx * nby)) << kBrickShift;
+    const size_t colp = (size_t)(X + kPadLo) + (size_t)V.px * (Y + kPadLo);
+#pragma unroll
+    for (int k = 0; k < 11; ++k) col[k] = __ldg(v + colp + (size_t)V.pxy * (min(Z0 - 1 + k, nz) + kPadLo));
+  };
+  if (t < 121 && (int)blockIdx.x < nwork) load_columns(blockIdx.x);
   for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
     const int bid = list ? list[1 + item] : item;
     const int bx = bid % nbx, by = (bid / nbx) % nby, bz = bid / (nbx * nby);
     const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
-    // stage: thread (i, j) loads the z column of [x0-1+i, y0-1+j]; coordinates beyond n
-    // are clamped to n (still inside the padded border, where E is the edge value)
     if (t < 121) {
-      const int i = t % 11, j = t / 11;
-      const int X = min(x0 - 1 + i, nx), Y = min(y0 - 1 + j, ny);
-      const int colp = (X + kPadLo) + V.px * (Y + kPadLo);
 #pragma unroll
-      for (int k = 0; k < 11; ++k) {
-        const int Z = min(z0 - 1 + k, nz);
-        tile[k][j][i] = ldv<VTYPE>(v, colp + V.pxy * (Z + kPadLo));
-      }
+      for (int k = 0; k < 11; ++k) tile[k][sj][si] = to_float<VTYPE>(col[k]);
+      if (item + (int)gridDim.x < nwork) load_columns(item + gridDim.x);
     }
     __syncthreads();
     const int x = x0 + u, y = y0 + w;
@@ -306,56 +370,39 @@ __global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* 
       } else {
         wr_lo = !(ox | oy);
       }
-      constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
-      constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
-      constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
-      float P[3][3][3];  // [z][y][x] neighbourhood of the current voxel, rolled along z
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-          for (int a = 0; a < 3; ++a) P[c][b][a] = tile[c][w + b][u + a];
       const int qn = min(kBrick + 1, nz - z0);
       float4* out = rec + (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z0);
       const size_t zstride = (size_t)nx * ny;
-      for (int q = 0; q < qn; ++q) {
+      if (wr_lo || (wr_top && qn > kBrick)) {
+        // per-plane sums of the 3x3 (x, y) neighbourhood; plane k is voxel z0 - 1 + k
+        PlaneSums ps[3];
+        ps[0] = plane_sums<OP>(tile[0], u, w);
+        ps[1] = plane_sums<OP>(tile[1], u, w);
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-          for (int a = 0; a < 3; ++a) P[2][b][a] = tile[q + 2][w + b][u + a];
-        if (q < kBrick ? wr_lo : wr_top) {
-          float g[3];
-          if constexpr (OP == OP_CENTRAL) {
-            g[0] = P[1][1][2] - P[1][1][0];
-            g[1] = P[1][2][1] - P[1][0][1];
-            g[2] = P[2][1][1] - P[0][1][1];
-          } else {
-            float d[3][3][3];  // difference planes along x ([z][y]), y ([z][x]), z ([y][x])
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-              for (int b = 0; b < 3; ++b) {
-                d[0][a][b] = P[a][b][2] - P[a][b][0];
-                d[1][a][b] = P[a][2][b] - P[a][0][b];
-                d[2][a][b] = P[2][a][b] - P[0][a][b];
-              }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const float edges = (d[c][0][1] + d[c][2][1]) + (d[c][1][0] + d[c][1][2]);
-              const float corners = (d[c][0][0] + d[c][0][2]) + (d[c][2][0] + d[c][2][2]);
-              g[c] = fmaf(w0, d[c][1][1], fmaf(w1, edges, w2 * corners));
+        for (int q = 0; q <= kBrick; ++q) {
+          if (q < qn && (q < kBrick ? wr_lo : wr_top)) {
+            ps[(q + 2) % 3] = plane_sums<OP>(tile[q + 2], u, w);
+            const PlaneSums& lo = ps[q % 3];
+            const PlaneSums& md = ps[(q + 1) % 3];
+            const PlaneSums& hi = ps[(q + 2) % 3];
+            float g[3];
+            if constexpr (OP == OP_CENTRAL) {
+              g[0] = md.ax;
+              g[1] = md.ay;
+              g[2] = hi.c - lo.c;
+            } else {
+              constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+              constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+              constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+              g[0] = fmaf(w0, md.ax, fmaf(w1, md.bx + (lo.ax + hi.ax), w2 * (lo.bx + hi.bx)));
+              g[1] = fmaf(w0, md.ay, fmaf(w1, md.by + (lo.ay + hi.ay), w2 * (lo.by + hi.by)));
+              g[2] = hi.q - lo.q;
             }
+            out[q * zstride] = make_float4(g[0], g[1], g[2], md.c);
+          } else if (q < qn) {
+            ps[(q + 2) % 3] = plane_sums<OP>(tile[q + 2], u, w);
           }
-          out[q * zstride] = make_float4(g[0], g[1], g[2], P[1][1][1]);
         }
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            P[0][b][a] = P[1][b][a];
-            P[1][b][a] = P[2][b][a];
-          }
       }
     }
     __syncthreads();  // the tile is restaged for the next brick
