@@ -201,8 +201,12 @@ struct TfSample {
   bool inside;  // u was not clamped (slope is defined)
 };
 
-// §3.7 lookup table read with linear interpolation between entries.
-__device__ __forceinline__ TfSample tf_lookup(const TfDev& tf, float s_raw) {
+// §3.7 lookup table read with linear interpolation between entries.  `table` is tf.tf or a
+// copy of it in shared memory (SHARED: plain loads, which the compiler issues as shared
+// loads when the pointer comes from a __shared__ array).
+template <bool SHARED = false>
+__device__ __forceinline__ TfSample tf_lookup(const TfDev& tf, float s_raw,
+                                              const float4* table = nullptr) {
   TfSample r;
   float u = s_raw * tf.scale;
   const float top = (float)(tf.n - 1);
@@ -212,7 +216,14 @@ __device__ __forceinline__ TfSample tf_lookup(const TfDev& tf, float s_raw) {
   if (i > tf.n - 2) i = tf.n - 2;
   r.i = i;
   r.w = u - (float)i;
-  const float4 a = __ldg(tf.tf + i), b = __ldg(tf.tf + i + 1);
+  float4 a, b;
+  if constexpr (SHARED) {
+    a = table[i];
+    b = table[i + 1];
+  } else {
+    a = __ldg(tf.tf + i);
+    b = __ldg(tf.tf + i + 1);
+  }
   r.rgba.x = lerpf(a.x, b.x, r.w);
   r.rgba.y = lerpf(a.y, b.y, r.w);
   r.rgba.z = lerpf(a.z, b.z, r.w);

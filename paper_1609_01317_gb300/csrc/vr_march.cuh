@@ -56,10 +56,12 @@ __device__ __forceinline__ void corners_gradient(const Corners& k, const Cell& c
 // all lie in invisible bricks jumps to the furthest of their brick exits: every sample in
 // between lies in one of those bricks (each lane's interval starts at its own sample and the
 // starts are consecutive), so nothing visible is skipped.
-template <bool CKPT>
+// TFS: the transfer function is read from s_tf, a copy in shared memory.
+template <bool CKPT, bool TFS = false>
 __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, bool active,
                                           int q, unsigned qmask, unsigned& hit, unsigned& plain,
-                                          unsigned& visited, unsigned& shaded) {
+                                          unsigned& visited, unsigned& shaded,
+                                          const float4* s_tf = nullptr) {
   const int W = L.cam.width, H = L.cam.height;
   const int ray = py * W + px;
   const int qbase = (threadIdx.x & 31) & ~3;
@@ -121,7 +123,7 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
       Corners cr;
       corners_load(L.R, c, cr);
       const float s = corners_value(cr, c);
-      const TfSample ts = tf_lookup(L.tf, s);
+      const TfSample ts = tf_lookup<TFS>(L.tf, s, s_tf);
       alpha = ts.rgba.w;
       if (alpha != 0.0f) {
         ++shaded;

@@ -18,8 +18,16 @@ namespace vr {
 constexpr int kThreads = 128;
 constexpr int kTileW = 4, kTileH = 2;  // one warp's pixels (a quad of lanes per ray)
 
-template <bool CKPT>
-__global__ void __launch_bounds__(kThreads) k_march(const MarchLaunch L) {
+constexpr int kMaxSharedTf = 1024;  // tables up to this many entries are copied to shared memory
+
+// TFS: the block copies the transfer function (n <= kMaxSharedTf entries) to shared memory.
+template <bool CKPT, bool TFS>
+__global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
+  extern __shared__ float4 s_tf[];
+  if constexpr (TFS) {
+    for (int i = threadIdx.x; i < L.tf.n; i += kThreads) s_tf[i] = L.tf.tf[i];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const int q = lane & 3, qd = lane >> 2;
   const unsigned qmask = 0xFu << (lane & ~3);
@@ -34,7 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_march(const MarchLaunch L) {
     if (tile >= tiles) break;
     const int px = (tile % tiles_x) * kTileW + (qd & 3);
     const int py = (tile / tiles_x) * kTileH + (qd >> 2);
-    march_ray<CKPT>(L, px, py, px < W && py < H, q, qmask, hit, plain, visited, shaded);
+    march_ray<CKPT, TFS>(L, px, py, px < W && py < H, q, qmask, hit, plain, visited, shaded, s_tf);
     __syncwarp();
   }
   if (L.stats) {
@@ -52,25 +60,31 @@ __global__ void __launch_bounds__(kThreads) k_march(const MarchLaunch L) {
 }
 
 // Blocks that keep every SM busy once (the kernel is persistent).
+template <bool CKPT, bool TFS>
+static int persistent_blocks(size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march<CKPT, TFS>, kThreads, smem);
+  return (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+}
+
 template <bool CKPT>
-static int persistent_blocks() {
-  static int cached = 0;
-  if (cached == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march<CKPT>, kThreads, 0);
-    cached = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+static void launch_march_k(const MarchLaunch& L, cudaStream_t s) {
+  if (L.tf.n <= kMaxSharedTf) {
+    const size_t smem = sizeof(float4) * (size_t)L.tf.n;
+    k_march<CKPT, true><<<persistent_blocks<CKPT, true>(smem), kThreads, smem, s>>>(L);
+  } else {
+    k_march<CKPT, false><<<persistent_blocks<CKPT, false>(0), kThreads, 0, s>>>(L);
   }
-  return cached;
 }
 
 cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s) {
   // the tile counter starts at zero for every launch
   cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  if (L.ck_kend) k_march<true><<<persistent_blocks<true>(), kThreads, 0, s>>>(L);
-  else k_march<false><<<persistent_blocks<false>(), kThreads, 0, s>>>(L);
+  if (L.ck_kend) launch_march_k<true>(L, s);
+  else launch_march_k<false>(L, s);
   return cudaGetLastError();
 }
 
