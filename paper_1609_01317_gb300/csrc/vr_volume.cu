@@ -323,7 +323,7 @@ template <int VTYPE, int OP>
 __global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* __restrict__ need,
                                                  const int* __restrict__ list,
                                                  float4* __restrict__ rec) {
-  __shared__ float tile[11][11][12];  // [z][y][x], x padded to 12
+  __shared__ __align__(16) float tile[11][11][12];  // [z][y][x], x padded to 12
   const int t = threadIdx.x;
   const int nbx = V.nb[0], nby = V.nb[1];
   const int nbricks = nbx * nby * V.nb[2];
@@ -332,30 +332,56 @@ __global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* 
   const int u = t % 9, w = t / 9;  // x, y offsets in the brick (threads below 81)
   const int nwork = list ? list[0] : nbricks;
   using T = typename VoxelT<VTYPE>::T;
-  // stage: thread (i, j) < 121 loads the z column of [x0-1+i, y0-1+j] of a brick;
-  // coordinates beyond n are clamped to n (still inside the padded border, where E is the
-  // edge value).  The next brick's columns are loaded into registers while the current one
-  // is computed.
-  const int si = t % 11, sj = t / 11;
-  T col[11];
-  auto load_columns = [&](int item) {
+  // stage: thread (j, k) < 121 loads padded row (y0-1+j, z0-1+k) from padded x = x0, i.e.
+  // voxels x0-1 .. x0+14, as one aligned 16-element vector (row pitches are multiples of
+  // 16 elements and x0 of 8; the vector ends inside the row); rows beyond n are clamped to
+  // n (still inside the padded border, where E is the edge value).  The next brick's rows
+  // are loaded into registers while the current one is computed.
+  constexpr int kWords = 16 * (int)sizeof(T) / 4;
+  const int sj = t % 11, sk = t / 11;
+  uint32_t raw[kWords];
+  auto load_row = [&](int item) {
     const int b = list ? list[1 + item] : item;
-    const int X = min(((b % nbx) << kBrickShift) - 1 + si, nx);
     const int Y = min((((b / nbx) % nby) << kBrickShift) - 1 + sj, ny);
-    const int Z0 = (b / (nbx * nby)) << kBrickShift;
-    const size_t colp = (size_t)(X + kPadLo) + (size_t)V.px * (Y + kPadLo);
+    const int Z = min(((b / (nbx * nby)) << kBrickShift) - 1 + sk, nz);
+    const T* row = v + (size_t)V.px * (Y + kPadLo) + (size_t)V.pxy * (Z + kPadLo) +
+                   ((b % nbx) << kBrickShift);
+    if constexpr (sizeof(T) == 1) {
+      const uint2 a0 = __ldg(reinterpret_cast<const uint2*>(row));
+      const uint2 a1 = __ldg(reinterpret_cast<const uint2*>(row) + 1);
+      raw[0] = a0.x; raw[1] = a0.y; raw[2] = a1.x; raw[3] = a1.y;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 11; ++k) col[k] = __ldg(v + colp + (size_t)V.pxy * (min(Z0 - 1 + k, nz) + kPadLo));
+      for (int q = 0; q < kWords / 4; ++q) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(row) + q);
+        raw[4 * q] = a.x; raw[4 * q + 1] = a.y; raw[4 * q + 2] = a.z; raw[4 * q + 3] = a.w;
+      }
+    }
   };
-  if (t < 121 && (int)blockIdx.x < nwork) load_columns(blockIdx.x);
+  if (t < 121 && (int)blockIdx.x < nwork) load_row(blockIdx.x);
   for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
     const int bid = list ? list[1 + item] : item;
     const int bx = bid % nbx, by = (bid / nbx) % nby, bz = bid / (nbx * nby);
     const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
     if (t < 121) {
+      float e[12];
 #pragma unroll
-      for (int k = 0; k < 11; ++k) tile[k][sj][si] = to_float<VTYPE>(col[k]);
-      if (item + (int)gridDim.x < nwork) load_columns(item + gridDim.x);
+      for (int i = 0; i < 12; ++i) {
+        if constexpr (sizeof(T) == 1) {
+          e[i] = (float)((raw[i >> 2] >> (8 * (i & 3))) & 0xffu);
+        } else if constexpr (sizeof(T) == 2) {
+          const unsigned short h = (unsigned short)((raw[i >> 1] >> (16 * (i & 1))) & 0xffffu);
+          if constexpr (VTYPE == VT_F16) e[i] = __half2float(__ushort_as_half(h));
+          else e[i] = (float)h;
+        } else {
+          e[i] = __uint_as_float(raw[i]);
+        }
+      }
+      float4* dst = reinterpret_cast<float4*>(&tile[sk][sj][0]);
+      dst[0] = make_float4(e[0], e[1], e[2], e[3]);
+      dst[1] = make_float4(e[4], e[5], e[6], e[7]);
+      dst[2] = make_float4(e[8], e[9], e[10], e[11]);
+      if (item + (int)gridDim.x < nwork) load_row(item + gridDim.x);
     }
     __syncthreads();
     const int x = x0 + u, y = y0 + w;
