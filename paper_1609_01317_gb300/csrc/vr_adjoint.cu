@@ -328,18 +328,31 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
   }
 }
 
-__global__ void k_tf_partial_reduce(const float* __restrict__ partial, int blocks, int n4,
-                                    float* __restrict__ grad_tf) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n4) return;
+// grad_tf[e] += sum over blocks b of partial[b][e].  A block takes 32 entries: its 8 warps
+// sum the rows b = w, w + 8, ... in order (coalesced across the entries), then warp 0 adds
+// the 8 partial sums in order -- the same summation order on every run.
+__global__ void __launch_bounds__(256) k_tf_partial_reduce(const float* __restrict__ partial,
+                                                           int blocks, int n4,
+                                                           float* __restrict__ grad_tf) {
+  __shared__ float part[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
   float v = 0.0f;
-  for (int b = 0; b < blocks; ++b) v += partial[(size_t)b * n4 + e];
-  grad_tf[e] += v;
+  if (e < n4)
+    for (int b = w; b < blocks; b += 8) v += partial[(size_t)b * n4 + e];
+  part[w][lane] = v;
+  __syncthreads();
+  if (w == 0 && e < n4) {
+    float sum = part[0][lane];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) sum += part[j][lane];
+    grad_tf[e] += sum;
+  }
 }
 
 cudaError_t launch_tf_partial_reduce(const float* partial, int blocks, int n4, float* grad_tf,
                                      cudaStream_t s) {
-  k_tf_partial_reduce<<<(n4 + 127) / 128, 128, 0, s>>>(partial, blocks, n4, grad_tf);
+  k_tf_partial_reduce<<<(n4 + 31) / 32, 256, 0, s>>>(partial, blocks, n4, grad_tf);
   return cudaGetLastError();
 }
 
