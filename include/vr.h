@@ -239,6 +239,19 @@ vr_status vr_batch_autotune(vr_batch *batch, void *stream, int *chosen);
 /* Release the batch (synchronises the device).  NULL is a no-op. */
 void vr_batch_destroy(vr_batch *batch);
 
+/* One-shot batched render: camera i of n is rendered from vols[vol_of_cam[i]] into outs[i]
+ * (H x W x 4 float32 device image, caller-owned) by one persistent launch over the
+ * concatenated tiles of every render, without building a graph -- the same pixels as n
+ * vr_render calls.  Rays are independent (§2.2), so renders of different volumes, sizes and
+ * voxel types share the launch.  vols[k] for k <= max(vol_of_cam) must hold a volume and a
+ * transfer function on one device; gradient records are brought up to date on `stream`.
+ * The launch tables live in vols[0]'s context: calls that name the same vols[0] must be
+ * issued on one stream (or ordered by the caller).  collect_stats must be 0.
+ * Errors: INVALID_ARG, STATE, UNSUPPORTED (different devices, stats), OUT_OF_MEMORY, CUDA. */
+vr_status vr_render_batch(vr_ctx *const *vols, const vr_camera *cams, const int *vol_of_cam,
+                          int n, const vr_render_params *params, float *const *outs,
+                          void *stream);
+
 /* Short English text of a status code (static storage). */
 const char *vr_status_string(vr_status status);
 

@@ -4,9 +4,9 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
 benchmark's CPU-baseline leg, never by the product package.  It shares no code with the
 CUDA path.  See the header of ``vr_oracle.c`` for the method and the readings it follows.
 
-Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` except the
-Zucker-Hummel weights, whose agreement with the paper's own operator is "parity unpinned"
-(the paper does not print that mask).
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` and
+``tests/test_oracle_surface_pins.py`` except the Zucker-Hummel weights, whose agreement with
+the paper's own operator is "parity unpinned" (the paper does not print that mask).
 """
 from __future__ import annotations
 
@@ -32,6 +32,14 @@ class Params(C.Structure):
     _fields_ = [("step", C.c_float), ("grad", C.c_int), ("ka", C.c_double), ("kd", C.c_double),
                 ("ks", C.c_double), ("shininess", C.c_double), ("light", C.c_double * 3),
                 ("headlight", C.c_int), ("ert_threshold", C.c_double),
+                ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3)]
+
+
+class SurfaceParams(C.Structure):
+    _fields_ = [("step", C.c_float), ("iso_lo", C.c_float), ("iso_hi", C.c_float),
+                ("refine", C.c_int), ("grad", C.c_int), ("ka", C.c_double), ("kd", C.c_double),
+                ("ks", C.c_double), ("shininess", C.c_double), ("light", C.c_double * 3),
+                ("headlight", C.c_int), ("color", C.c_double * 3),
                 ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3)]
 
 
@@ -70,6 +78,12 @@ def lib():
                                         C.POINTER(C.c_int), C.c_int, dp, C.POINTER(C.c_int),
                                         C.c_int]
         L.vro_num_threads.restype = C.c_int
+        L.vro_sample_f32.restype = C.c_float
+        L.vro_sample_f32.argtypes = [C.POINTER(Volume), C.POINTER(C.c_float)]
+        L.vro_render_surface.restype = C.c_longlong
+        L.vro_render_surface.argtypes = [C.POINTER(Volume), C.POINTER(Camera),
+                                         C.POINTER(SurfaceParams), dp, C.POINTER(C.c_float),
+                                         C.c_int, C.c_int, C.c_int]
         L.vro_render_backward.argtypes = [C.POINTER(Volume), dp, C.c_int, C.POINTER(Camera),
                                           C.POINTER(Params), dp, dp, dp]
         _lib = L
@@ -197,3 +211,33 @@ def render_backward(ov: OracleVolume, tf, cam: dict, params: Params, grad_rgba):
 
 def num_threads() -> int:
     return lib().vro_num_threads()
+
+
+def make_surface_params(step=2.0, iso_lo=0.5, iso_hi=1e30, refine=6, grad="central", ka=0.1,
+                        kd=0.7, ks=0.2, shininess=20.0, light=(0.0, 0.0, 0.0), headlight=True,
+                        color=(1.0, 1.0, 1.0), clip_lo=(-1e30, -1e30, -1e30),
+                        clip_hi=(1e30, 1e30, 1e30)) -> SurfaceParams:
+    g = GRAD[grad] if isinstance(grad, str) else int(grad)
+    return SurfaceParams(float(step), float(iso_lo), float(iso_hi), int(refine), g, ka, kd, ks,
+                         shininess, (C.c_double * 3)(*light), int(bool(headlight)),
+                         (C.c_double * 3)(*color), (C.c_float * 3)(*clip_lo),
+                         (C.c_float * 3)(*clip_hi))
+
+
+def sample_f32(ov: OracleVolume, p) -> float:
+    """FP32 trilinear value in raw units (the inside test of the first-hit renderer)."""
+    pf = (C.c_float * 3)(*[float(v) for v in p])
+    return float(lib().vro_sample_f32(C.byref(ov.s), pf))
+
+
+def render_surface(ov: OracleVolume, cam: dict, sp: SurfaceParams, rows=None, nthreads=0):
+    """First-hit renderer (§3.11 threshold window, §5.1 refinement): returns (rgba (H, W, 4)
+    float64, depth (H, W) float32, coarse samples)."""
+    H, W = cam["height"], cam["width"]
+    r0, r1 = (0, H) if rows is None else rows
+    img = np.zeros((H, W, 4), np.float64)
+    depth = np.full((H, W), np.inf, np.float32)
+    c = make_camera(cam)
+    n = lib().vro_render_surface(C.byref(ov.s), C.byref(c), C.byref(sp), _dptr(img),
+                                 depth.ctypes.data_as(C.POINTER(C.c_float)), r0, r1, nthreads)
+    return img, depth, int(n)

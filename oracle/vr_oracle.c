@@ -53,6 +53,25 @@
  *   R9 front to back: C += T a c, T *= (1 - a); stop after the sample where 1 - T >= ert
  *      ("until an alpha of 0 is hit" read as transmittance -> 0).  Output (C, 1 - T),
  *      premultiplied over black.  Shading is skipped where a == 0 (it adds nothing).
+ *
+ * First-hit surfaces (the renderer the paper itself implements, §3.11, with the hitpoint
+ * refinement of §5.1):
+ *   R13 a threshold window [lo, hi] of raw voxel values marks solid matter; the coarse
+ *      samples are the samples of R4 with the coarse step; the first one inside the window
+ *      is the hit.  The inside tests decide integers and branches, so they are evaluated in
+ *      FP32 (the paper's precision) as: t_k = fma(k + 1/2, step, t_near),
+ *      p = fma(t, d, o) per axis, i0 = clamp(floor(p), 0, n - 2), f = p - i0, trilinear of
+ *      the raw values with lerps fma(f, b - a, a) along x, then y, then z; inside iff
+ *      lo <= s <= hi.
+ *   R14 refinement (§5.1: step back half a step, then halve the step, moving back while
+ *      inside and forward while outside, 5-6 times) = bisection of [a, b] = [t_{k-1}, t_k]
+ *      ([t_near, t_0] for k = 0) keeping a outside and b inside, m = (a + b) * 1/2 in FP32,
+ *      `refine` steps; the hit is the midpoint of the final bracket.  If k = 0 and the
+ *      entry point itself is inside, the hit is the entry point.
+ *   R15 at the hit point p = o + t d (FP64 from here on): N = -g/|g| (R7, R8) turned to face
+ *      the viewer (N.d <= 0, so surfaces entered from either side of the window are lit);
+ *      L, V and Phong as R8 with the surface colour; output (c, 1) and the depth t; a ray
+ *      without a hit gives (0, 0, 0, 0) and depth +inf.
  */
 #include <math.h>
 #include <stdint.h>
@@ -511,6 +530,135 @@ long long vro_render_pixels(const vro_volume *vol, const double *tf, int ntf,
         if (counts) counts[i] = k;
         total += k;
     }
+    return total;
+}
+
+/* ------------------------------------------------------------ first-hit surfaces */
+typedef struct {
+    float step, iso_lo, iso_hi;
+    int refine, grad;
+    double ka, kd, ks, shininess;
+    double light[3];
+    int headlight;
+    double color[3];
+    float clip_lo[3], clip_hi[3];
+} vro_surface_params;
+
+/* Raw voxel value at the clamp-to-edge position, as FP32. */
+static float raw_f32(const vro_volume *vol, int x, int y, int z)
+{
+    x = clampi(x, 0, vol->n[0] - 1);
+    y = clampi(y, 0, vol->n[1] - 1);
+    z = clampi(z, 0, vol->n[2] - 1);
+    return (float)raw_at(vol, (long)x + (long)vol->n[0] * ((long)y + (long)vol->n[1] * (long)z));
+}
+
+static float lerp_f32(float a, float b, float f) { return fmaf(f, b - a, a); }
+
+/* Reading R13: the FP32 trilinear value (raw units) that decides inside / outside. */
+float vro_sample_f32(const vro_volume *vol, const float p[3])
+{
+    int i[3];
+    float f[3];
+    for (int a = 0; a < 3; ++a) {
+        int top = vol->n[a] > 1 ? vol->n[a] - 2 : 0;
+        i[a] = clampi((int)floorf(p[a]), 0, top);
+        f[a] = p[a] - (float)i[a];
+    }
+    float c000 = raw_f32(vol, i[0], i[1], i[2]), c100 = raw_f32(vol, i[0] + 1, i[1], i[2]);
+    float c010 = raw_f32(vol, i[0], i[1] + 1, i[2]), c110 = raw_f32(vol, i[0] + 1, i[1] + 1, i[2]);
+    float c001 = raw_f32(vol, i[0], i[1], i[2] + 1), c101 = raw_f32(vol, i[0] + 1, i[1], i[2] + 1);
+    float c011 = raw_f32(vol, i[0], i[1] + 1, i[2] + 1);
+    float c111 = raw_f32(vol, i[0] + 1, i[1] + 1, i[2] + 1);
+    float x00 = lerp_f32(c000, c100, f[0]), x10 = lerp_f32(c010, c110, f[0]);
+    float x01 = lerp_f32(c001, c101, f[0]), x11 = lerp_f32(c011, c111, f[0]);
+    float y0 = lerp_f32(x00, x10, f[1]), y1 = lerp_f32(x01, x11, f[1]);
+    return lerp_f32(y0, y1, f[2]);
+}
+
+static int inside_at(const vro_volume *vol, const vro_surface_params *sp, const float o[3],
+                     const float d[3], float t)
+{
+    float p[3];
+    for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
+    float s = vro_sample_f32(vol, p);
+    return s >= sp->iso_lo && s <= sp->iso_hi;
+}
+
+/* One ray of the first-hit renderer (R13-R15).  Returns the coarse samples taken. */
+static int surface_pixel(const vro_volume *vol, const vro_basis *b, const float lo[3],
+                         const float hi[3], const vro_surface_params *sp, int px, int py,
+                         double out[4], float *depth)
+{
+    float o[3], d[3], tn;
+    int K;
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    *depth = INFINITY;
+    if (!ray_setup(b, lo, hi, sp->step, px, py, o, d, &tn, &K)) return 0;
+    int k;
+    for (k = 0; k < K; ++k)
+        if (inside_at(vol, sp, o, d, fmaf((float)k + 0.5f, sp->step, tn))) break;
+    if (k == K) return K;
+    float t_hit;
+    if (k == 0 && inside_at(vol, sp, o, d, tn)) {
+        t_hit = tn;
+    } else {
+        float ta = k == 0 ? tn : fmaf((float)k - 0.5f, sp->step, tn);
+        float tb = fmaf((float)k + 0.5f, sp->step, tn);
+        for (int r = 0; r < sp->refine; ++r) {
+            float m = 0.5f * (ta + tb);
+            if (inside_at(vol, sp, o, d, m)) tb = m;
+            else ta = m;
+        }
+        t_hit = 0.5f * (ta + tb);
+    }
+    *depth = t_hit;
+    double p[3], g[3], N[3], gn, L[3], V[3], c[3], lp[3], lv[3], ev[3];
+    for (int a = 0; a < 3; ++a) p[a] = (double)o[a] + (double)t_hit * (double)d[a];
+    vro_gradient(vol, sp->grad, p, g);
+    normal_from_gradient(g, N, &gn);
+    if (N[0] * d[0] + N[1] * d[1] + N[2] * d[2] > 0.0)
+        for (int a = 0; a < 3; ++a) N[a] = -N[a];
+    for (int a = 0; a < 3; ++a) lp[a] = sp->headlight ? (double)b->eye[a] : sp->light[a];
+    for (int a = 0; a < 3; ++a) lv[a] = lp[a] - p[a];
+    normalize3(lv, L);
+    if (b->ortho) {
+        for (int a = 0; a < 3; ++a) V[a] = -(double)d[a];
+    } else {
+        for (int a = 0; a < 3; ++a) ev[a] = (double)b->eye[a] - p[a];
+        normalize3(ev, V);
+    }
+    vro_shade(N, L, V, sp->color, sp->ka, sp->kd, sp->ks, sp->shininess, c);
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = 1.0;
+    return k + 1;
+}
+
+/* Render rows [row0, row1) with the first-hit renderer; depth (H x W) receives the hit
+ * distance along the unit ray (+inf where nothing is hit).  Returns the coarse samples. */
+long long vro_render_surface(const vro_volume *vol, const vro_camera *cam,
+                             const vro_surface_params *sp, double *out_rgba, float *depth,
+                             int row0, int row1, int nthreads)
+{
+    vro_basis b;
+    float lo[3], hi[3];
+    vro_params box;
+    camera_basis(cam, &b);
+    for (int a = 0; a < 3; ++a) {
+        box.clip_lo[a] = sp->clip_lo[a];
+        box.clip_hi[a] = sp->clip_hi[a];
+    }
+    render_box(&box, vol->n, lo, hi);
+    long long total = 0;
+    int W = cam->width;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
+#endif
+    for (int py = row0; py < row1; ++py)
+        for (int px = 0; px < W; ++px) {
+            long pix = (long)py * W + px;
+            total += surface_pixel(vol, &b, lo, hi, sp, px, py, out_rgba + 4 * pix, depth + pix);
+        }
     return total;
 }
 

@@ -355,6 +355,7 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->out_staging);
   ctx_free(ctx, ctx->adj);
   ctx_free(ctx, ctx->tf_partial);
+  ctx_free(ctx, ctx->batch_tab);
   ctx_free(ctx, ctx->rec);
   delete ctx;
 }

@@ -334,6 +334,90 @@ vr_status vr_batch_autotune(vr_batch* b, void* stream, int* chosen) {
   return st;
 }
 
+vr_status vr_render_batch(vr_ctx* const* vols, const vr_camera* cams, const int* vol_of_cam,
+                          int n, const vr_render_params* params, float* const* outs,
+                          void* stream) {
+  if (!vols || !cams || !vol_of_cam || n < 1 || !outs) return VR_ERR_INVALID_ARG;
+  vr_status st = check_params(params);
+  if (st != VR_OK) return st;
+  if (params->collect_stats) return VR_ERR_UNSUPPORTED;
+  int nvol = 0;
+  for (int i = 0; i < n; ++i) {
+    if (vol_of_cam[i] < 0 || !outs[i]) return VR_ERR_INVALID_ARG;
+    nvol = std::max(nvol, vol_of_cam[i] + 1);
+  }
+  for (int i = 0; i < nvol; ++i) {
+    if (!vols[i]) return VR_ERR_INVALID_ARG;
+    if (!vols[i]->has_volume || !vols[i]->has_tf) return VR_ERR_STATE;
+    if (vols[i]->device != vols[0]->device) return VR_ERR_UNSUPPORTED;
+  }
+  std::vector<MarchLaunch> items(n);
+  for (int i = 0; i < n; ++i) {
+    CamDev basis;
+    st = check_camera(&cams[i], &basis);
+    if (st != VR_OK) return st;
+    std::memset(&items[i], 0, sizeof(MarchLaunch));
+    items[i].cam = basis;
+  }
+  vr_ctx* owner = vols[0];
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != owner->device) cudaSetDevice(owner->device);
+  struct Restore {
+    int p, d;
+    ~Restore() {
+      if (p >= 0 && p != d) cudaSetDevice(p);
+    }
+  } restore{prev, owner->device};
+  for (int i = 0; i < n; ++i)
+    if (!is_device_pointer(outs[i])) return VR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < nvol; ++i) {
+    st = ensure_records(vols[i], params, s);
+    if (st != VR_OK) return st;
+  }
+  // descriptors and tile prefix sums, copied into the owner's table buffer on `stream`
+  constexpr int tw = 4, th = 2;
+  std::vector<int> pre(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    vr_ctx* c = vols[vol_of_cam[i]];
+    MarchLaunch& L = items[i];
+    L.V = vol_dev(c);
+    L.R = rec_dev(c);
+    L.tf = tf_dev(c);
+    L.r = render_dev(c, params);
+    L.dtype = (int)c->dtype;
+    L.op = params->grad;
+    L.out = reinterpret_cast<float4*>(outs[i]);
+    const long long t = (long long)((L.cam.width + tw - 1) / tw) * ((L.cam.height + th - 1) / th);
+    if ((long long)pre[i] + t > 2000000000LL) return VR_ERR_INVALID_ARG;
+    pre[i + 1] = pre[i] + (int)t;
+  }
+  const size_t items_bytes = (sizeof(MarchLaunch) * n + 255) / 256 * 256;
+  const size_t prefix_bytes = (sizeof(int) * (n + 1) + 255) / 256 * 256;
+  st = ensure(owner, &owner->batch_tab, &owner->batch_tab_cap, items_bytes + prefix_bytes + 256);
+  if (st != VR_OK) return st;
+  char* tab = static_cast<char*>(owner->batch_tab);
+  st = cuda_status(cudaMemcpyAsync(tab, items.data(), sizeof(MarchLaunch) * n,
+                                   cudaMemcpyHostToDevice, s));
+  if (st == VR_OK)
+    st = cuda_status(cudaMemcpyAsync(tab + items_bytes, pre.data(), sizeof(int) * (n + 1),
+                                     cudaMemcpyHostToDevice, s));
+  if (st != VR_OK) return st;
+  BatchLaunch B;
+  B.items = reinterpret_cast<const MarchLaunch*>(tab);
+  B.prefix = reinterpret_cast<const int*>(tab + items_bytes);
+  B.nitems = n;
+  B.tiles_total = pre[n];
+  B.counter = reinterpret_cast<unsigned*>(tab + items_bytes + prefix_bytes);
+  B.tw = tw;
+  B.th = th;
+  st = cuda_status(cudaMemsetAsync(B.counter, 0, sizeof(unsigned), s));
+  if (st != VR_OK) return st;
+  k_march_batch<128><<<batch_blocks(128), 128, 0, s>>>(B);
+  return cuda_status(cudaGetLastError());
+}
+
 void vr_batch_destroy(vr_batch* b) {
   if (!b) return;
   int prev = -1;

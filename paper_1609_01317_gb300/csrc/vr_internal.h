@@ -77,6 +77,10 @@ struct vr_ctx {
   float* tf_partial = nullptr;
   size_t tf_partial_cap = 0;
 
+  // tables of one-shot batched renders issued with this context first (vr_render_batch)
+  void* batch_tab = nullptr;
+  size_t batch_tab_cap = 0;
+
   // operator gradient records (G, V) per voxel and what they were computed for
   float4* rec = nullptr;
   size_t rec_cap = 0;

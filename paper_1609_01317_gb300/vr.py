@@ -79,6 +79,9 @@ _SIGS = [
     ("vr_batch_run", C.c_int, [C.c_void_p, C.c_void_p]),
     ("vr_batch_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     ("vr_batch_destroy", None, [C.c_void_p]),
+    ("vr_render_batch", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(vr_camera), C.POINTER(C.c_int),
+                                  C.c_int, C.POINTER(vr_render_params), C.POINTER(C.c_void_p),
+                                  C.c_void_p]),
     ("vr_status_string", C.c_char_p, [C.c_int]),
     ("vr_last_cuda_error", C.c_char_p, []),
     ("vr_version", C.c_int, []),
@@ -243,6 +246,16 @@ def vr_batch_autotune(batch, stream=None):
 
 def vr_batch_destroy(batch):
     lib().vr_batch_destroy(batch)
+
+
+def vr_render_batch(vols, cams, vol_of_cam, params, outs, stream=None):
+    n = len(cams)
+    varr = (C.c_void_p * len(vols))(*vols)
+    cams_arr = (vr_camera * n)(*[c if isinstance(c, vr_camera) else make_camera(c) for c in cams])
+    idx = (C.c_int * n)(*[int(i) for i in vol_of_cam])
+    oarr = (C.c_void_p * n)(*[_ptr(o) for o in outs])
+    _check("vr_render_batch", lib().vr_render_batch(varr, cams_arr, idx, n, C.byref(params), oarr,
+                                                    stream))
 
 
 def vr_status_string(status) -> str:

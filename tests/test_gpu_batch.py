@@ -68,3 +68,42 @@ def test_batch_matches_single_renders_and_autotunes():
         torch.cuda.synchronize()
         for r in rends:
             r.close()
+
+
+def test_one_shot_render_batch_matches_single_renders():
+    import torch
+    from paper_1609_01317_gb300 import Renderer, build, vr
+
+    build.build()
+    shapes = [((20, 26, 18), np.uint16, 4095.0), ((31, 22, 27), np.uint8, 255.0)]
+    rends = []
+    for i, (shp, dt, vmax) in enumerate(shapes):
+        r = Renderer(0)
+        r.upload_volume(P.ellipsoids(400 + i, shp, value_max=vmax, dtype=dt), vmax)
+        r.set_transfer_function(P.tf_random(500 + i, 48, alpha_max=0.4, zero_below=6))
+        rends.append(r)
+    cams, owner = [], []
+    for i, (shp, _, _) in enumerate(shapes):
+        for c in P.seeded_orbit_cameras(600 + i, shp, 4, 37 + 5 * i, 29):
+            cams.append(c)
+            owner.append(i)
+    try:
+        for grad in ("central", "zucker_hummel"):
+            params = vr.make_params(grad=grad, skip_empty=True)
+            refs = []
+            for c, o in zip(cams, owner):
+                rends[o].set_camera(c)
+                refs.append(rends[o].render(params=params).clone())
+            outs = [torch.full_like(r, float("nan")) for r in refs]
+            vr.vr_render_batch([r.ctx for r in rends], cams, owner, params, outs,
+                               torch.cuda.current_stream().cuda_stream or None)
+            torch.cuda.synchronize()
+            for o, ref in zip(outs, refs):
+                assert torch.equal(o, ref)
+        with pytest.raises(vr.VrError) as e:
+            vr.vr_render_batch([r.ctx for r in rends], cams, [0] * (len(cams) - 1) + [-1],
+                               params, outs)
+        assert e.value.status == 1
+    finally:
+        for r in rends:
+            r.close()
