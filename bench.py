@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--workload", choices=["ct", "ellipsoids", "sphere"], default="ct")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch"], default="main",
+    ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch", "surface"], default="main",
                     help="run one leg alone and print its JSON (for profiling)")
     ap.add_argument("--source-hash", choices=sorted(KERNEL_SOURCES),
                     help="print the source hash recorded beside a kernel's ncu counters")
@@ -381,6 +381,48 @@ def batch_leg(args):
             "renders_per_s": n / (t_b / 1e3), "phantom_generation_s": gen_s}
 
 
+def surface_leg(R, args):
+    """First-hit surface renderer (§3.11, §5.1) on the CT workload's volume and camera:
+    bone window [2200, 4095], coarse step 2.0 (four times the direct renderer's step), six
+    bisection steps, Zucker-Hummel normal, skipping on; the volume stays resident."""
+    import torch
+
+    import phantoms as P
+    from paper_1609_01317_gb300 import vr
+
+    w = P.workload_ct()
+    vol = w["volume"]
+    nz, ny, nx = vol.shape
+    ctx = R.ctx
+    sh = torch.cuda.current_stream().cuda_stream or None
+    vol_dev = torch.from_numpy(vol.view(np.int16)).cuda()
+    vr.vr_upload_volume(ctx, vol_dev, "u16", nx, ny, nz, w["value_max"], sh)
+    cam = w["camera"]
+    vr.vr_set_camera(ctx, vr.make_camera(cam))
+    H, W = cam["height"], cam["width"]
+    img = torch.empty((H, W, 4), device="cuda")
+    depth = torch.empty((H, W), device="cuda")
+    p = vr.make_surface_params(step=2.0, iso_lo=2200.0, iso_hi=4095.0, refine=6,
+                               grad="zucker_hummel", skip_empty=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        vr.vr_render_surface(ctx, p, img, depth, sh)
+    reps = max(10, min(args.steps, 100))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps)]
+    for i in range(reps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        vr.vr_render_surface(ctx, p, img, depth, sh)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    hits = int(torch.isfinite(depth).sum().item())
+    return {"workload": "ct512x512x361_u16_persp1920x1080_bone_surface",
+            "window": [2200.0, 4095.0], "step": 2.0, "refine": 6, "grad": "zucker_hummel",
+            "ms_per_frame": ms, "frames_per_s": 1000.0 / ms,
+            "mrays_per_s": H * W / (ms / 1e3) / 1e6, "rays_hit": hits}
+
+
 def fwd_bwd_leg(R, args):
     """Differentiable workload: 128^3 float32 blurred density, learnable 256-entry TF,
     16 views at 256x256, central differences, step 0.5.  Times the forward that records
@@ -572,6 +614,7 @@ def run_ours(args):
 
     if not args.no_extras:
         line["fwd_bwd"] = fwd_bwd_leg(R, args)
+        line["surface"] = surface_leg(R, args)
         line["batch"] = batch_leg(args)
     if not args.no_extras and world == 1:
         # end to end through the C ABI with host buffers: H2D of the volume and TF, D2H of
@@ -627,9 +670,9 @@ def run_leg(args):
 
     build.build()
     torch.cuda.set_device(0)
-    if args.leg == "fwd_bwd":
+    if args.leg in ("fwd_bwd", "surface"):
         R = Renderer(0)
-        out = fwd_bwd_leg(R, args)
+        out = (fwd_bwd_leg if args.leg == "fwd_bwd" else surface_leg)(R, args)
         R.close()
     else:
         out = batch_leg(args)

@@ -168,6 +168,43 @@ vr_status vr_render_backward(vr_ctx *ctx, const vr_render_params *params,
                              const void *checkpoints, const float *grad_rgba,
                              float *grad_volume, float *grad_tf, void *stream);
 
+/* First-hit surface rendering -- the renderer the paper itself implements (§3.11): a
+ * threshold window [iso_lo, iso_hi] of raw voxel values marks solid matter; each ray takes
+ * coarse samples t_k = t_near + (k + 1/2) step (the sample grid of vr_render with this step)
+ * until the first one whose trilinear value lies in the window, then refines the hit by
+ * bisection between the previous sample (the entry point for k = 0) and that one, keeping
+ * the outside end outside and the inside end inside, `refine` times (§5.1 hitpoint
+ * refinement: 5-6 steps locate the surface 32-64 times more precisely, so the coarse step
+ * can be 4-5 times the direct-rendering step); the hit is the middle of the final bracket,
+ * or the entry point itself when that is already inside.  The inside tests run in FP32
+ * exactly as: t = fma(k + 1/2, step, t_near), p = fma(t, d, o), cell and trilinear lerps
+ * fma(f, b - a, a) along x, then y, then z; bisection midpoints (a + b) * 1/2.
+ * At the hit, the operator gradient (§3.5) gives N = -g/|g|, turned to face the viewer, and
+ * Phong (§3.8, as vr_render) with the surface colour gives the pixel (c, 1); rays without a
+ * hit give (0, 0, 0, 0).  The output is H x W x 4 float32 (device or host memory);
+ * out_depth (optional, NULL to skip; device or host) receives H x W float32 hit distances t
+ * along the unit ray direction from the ray origin, +inf where nothing is hit.
+ * skip_empty: coarse samples in 8^3 bricks (and 32^3 macro bricks) whose footprint value
+ * range misses the window are skipped; this never changes a pixel.
+ * Needs a volume and a camera (no transfer function).
+ * Errors: INVALID_ARG (NULL params or output, step <= 0, iso_lo > iso_hi or NaN,
+ * refine outside [0, 24], invalid shading parameters), STATE, OUT_OF_MEMORY, CUDA. */
+typedef struct {
+  float step;            /* coarse sample spacing (voxel units, > 0) */
+  float iso_lo, iso_hi;  /* threshold window in raw voxel units, inclusive */
+  int refine;            /* bisection steps after the first hit, 0..24 */
+  vr_grad grad;
+  float ka, kd, ks, shininess;
+  float light[3];
+  int headlight;
+  float color[3];        /* surface colour */
+  int skip_empty;
+  float clip_lo[3], clip_hi[3];
+} vr_surface_params;
+
+vr_status vr_render_surface(vr_ctx *ctx, const vr_surface_params *params, float *out_rgba,
+                            float *out_depth, void *stream);
+
 /* Render without allocating any device memory.  (The paper has no counterpart: this entry
  * exists for callers that cannot allocate device memory when they render -- a plug-in
  * inside an application that owns the device's whole memory pool, a real-time loop that

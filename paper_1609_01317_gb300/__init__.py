@@ -143,6 +143,20 @@ class Renderer:
         vr.vr_render(self.ctx, p, out, _stream_handle())
         return out
 
+    def render_surface(self, params=None, out=None, depth=None, **kw):
+        """First-hit surface render of the current volume and camera (§3.11, §5.1); returns
+        ((H, W, 4) float32 image, (H, W) float32 hit distances, +inf where nothing is hit)."""
+        torch = _torch()
+        p = params if params is not None else vr.make_surface_params(**kw)
+        H, W = self.camera["height"], self.camera["width"]
+        dev = f"cuda:{self.device}"
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+        if depth is None:
+            depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+        vr.vr_render_surface(self.ctx, p, out, depth, _stream_handle())
+        return out, depth
+
     def stats(self) -> dict:
         return vr.vr_read_stats(self.ctx, _stream_handle())
 

@@ -356,6 +356,7 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->adj);
   ctx_free(ctx, ctx->tf_partial);
   ctx_free(ctx, ctx->batch_tab);
+  ctx_free(ctx, ctx->surf_vis);
   ctx_free(ctx, ctx->rec);
   delete ctx;
 }

@@ -62,7 +62,8 @@ struct vr_ctx {
   vr_camera cam{};
   vr::CamDev camdev{};
 
-  // statistics (4 counters) followed by the march's tile counter
+  // statistics: [0..3] counters, then the tile counters of the march [4], the adjoint [5]
+  // and the surface renderer [6]
   unsigned long long* stats = nullptr;
   bool stats_valid = false;
 
@@ -76,6 +77,10 @@ struct vr_ctx {
   // per-block partial sums of the transfer-function gradient, [blocks][4 * ntf]
   float* tf_partial = nullptr;
   size_t tf_partial_cap = 0;
+
+  // brick and macro-brick visibility for a surface render's threshold window
+  void* surf_vis = nullptr;
+  size_t surf_vis_cap = 0;
 
   // tables of one-shot batched renders issued with this context first (vr_render_batch)
   void* batch_tab = nullptr;

@@ -41,6 +41,14 @@ class vr_render_params(C.Structure):
                 ("collect_stats", C.c_int)]
 
 
+class vr_surface_params(C.Structure):
+    _fields_ = [("step", C.c_float), ("iso_lo", C.c_float), ("iso_hi", C.c_float),
+                ("refine", C.c_int), ("grad", C.c_int), ("ka", C.c_float), ("kd", C.c_float),
+                ("ks", C.c_float), ("shininess", C.c_float), ("light", C.c_float * 3),
+                ("headlight", C.c_int), ("color", C.c_float * 3), ("skip_empty", C.c_int),
+                ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3)]
+
+
 class vr_stats(C.Structure):
     _fields_ = [("rays_hit", C.c_ulonglong), ("samples_plain", C.c_ulonglong),
                 ("samples_visited", C.c_ulonglong), ("samples_shaded", C.c_ulonglong)]
@@ -79,6 +87,8 @@ _SIGS = [
     ("vr_batch_run", C.c_int, [C.c_void_p, C.c_void_p]),
     ("vr_batch_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     ("vr_batch_destroy", None, [C.c_void_p]),
+    ("vr_render_surface", C.c_int, [C.c_void_p, C.POINTER(vr_surface_params), C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
     ("vr_render_batch", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(vr_camera), C.POINTER(C.c_int),
                                   C.c_int, C.POINTER(vr_render_params), C.POINTER(C.c_void_p),
                                   C.c_void_p]),
@@ -142,6 +152,17 @@ def make_params(step=0.5, grad="central", ka=0.1, kd=0.7, ks=0.2, shininess=20.0
                             (C.c_float * 3)(*light), int(bool(headlight)), float(ert_threshold),
                             int(bool(skip_empty)), (C.c_float * 3)(*clip_lo),
                             (C.c_float * 3)(*clip_hi), int(bool(collect_stats)))
+
+
+def make_surface_params(step=2.0, iso_lo=0.5, iso_hi=3.0e38, refine=6, grad="central", ka=0.1,
+                        kd=0.7, ks=0.2, shininess=20.0, light=(0.0, 0.0, 0.0), headlight=True,
+                        color=(1.0, 1.0, 1.0), skip_empty=True, clip_lo=(-1e30, -1e30, -1e30),
+                        clip_hi=(1e30, 1e30, 1e30)) -> vr_surface_params:
+    g = GRADS[grad] if isinstance(grad, str) else int(grad)
+    return vr_surface_params(float(step), float(iso_lo), float(iso_hi), int(refine), g, float(ka),
+                             float(kd), float(ks), float(shininess), (C.c_float * 3)(*light),
+                             int(bool(headlight)), (C.c_float * 3)(*color), int(bool(skip_empty)),
+                             (C.c_float * 3)(*clip_lo), (C.c_float * 3)(*clip_hi))
 
 
 # ----------------------------------------------------------- same-name wrappers
@@ -246,6 +267,11 @@ def vr_batch_autotune(batch, stream=None):
 
 def vr_batch_destroy(batch):
     lib().vr_batch_destroy(batch)
+
+
+def vr_render_surface(ctx, params, out_rgba, out_depth=None, stream=None):
+    _check("vr_render_surface", lib().vr_render_surface(ctx, C.byref(params), _ptr(out_rgba),
+                                                        _ptr(out_depth), stream))
 
 
 def vr_render_batch(vols, cams, vol_of_cam, params, outs, stream=None):
