@@ -350,6 +350,7 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->vol);
   ctx_free(ctx, ctx->brick_minmax);
   ctx_free(ctx, ctx->upload_staging);
+  if (ctx->host_copy_done) cudaEventDestroy(ctx->host_copy_done);
   ctx_free(ctx, ctx->tf);
   ctx_free(ctx, ctx->stats);
   ctx_free(ctx, ctx->out_staging);
@@ -359,6 +360,16 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->surf_vis);
   ctx_free(ctx, ctx->rec);
   delete ctx;
+}
+
+// Record the end of a copy from a caller's host buffer on `s` (waited for before returning).
+static vr_status mark_host_copy(vr_ctx* ctx, cudaStream_t s) {
+  if (!ctx->host_copy_done) {
+    const vr_status st =
+        cuda_status(cudaEventCreateWithFlags(&ctx->host_copy_done, cudaEventDisableTiming));
+    if (st != VR_OK) return st;
+  }
+  return cuda_status(cudaEventRecord(ctx->host_copy_done, s));
 }
 
 vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int nx, int ny,
@@ -384,6 +395,8 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
     if (st != VR_OK) return st;
     st = cuda_status(cudaMemcpyAsync(ctx->upload_staging, voxels, (size_t)nvox * eb,
                                      cudaMemcpyHostToDevice, s));
+    if (st != VR_OK) return st;
+    st = mark_host_copy(ctx, s);
     if (st != VR_OK) return st;
     src = ctx->upload_staging;
   }
@@ -430,9 +443,9 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
   st = refresh_visibility(ctx, s);
   if (st != VR_OK) return st;
   if (!is_device_pointer(voxels)) {
-    // the staging copy is read by the padding kernel: keep the host buffer's contract
-    // ("read before the call returns") by waiting for the H2D copy.
-    st = cuda_status(cudaStreamSynchronize(s));
+    // keep the host buffer's contract ("read before the call returns"): wait for the
+    // host-to-device copy only; the padding and brick kernels stay queued on the stream.
+    st = cuda_status(cudaEventSynchronize(ctx->host_copy_done));
   }
   return st;
 }
@@ -452,13 +465,18 @@ vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, void* 
   st = cuda_status(cudaMemcpyAsync(ctx->tf, rgba, (size_t)n * sizeof(float4),
                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   if (st != VR_OK) return st;
+  if (!dev) {
+    st = mark_host_copy(ctx, s);
+    if (st != VR_OK) return st;
+  }
   st = cuda_status(launch_tf_prefix(ctx->tf, n, ctx->tf_prefix, s));
   if (st != VR_OK) return st;
   ctx->ntf = n;
   ctx->has_tf = true;
   ++ctx->tf_gen;
   st = refresh_visibility(ctx, s);
-  if (st == VR_OK && !dev) st = cuda_status(cudaStreamSynchronize(s));
+  // the caller's host table has been read once the copy is done
+  if (st == VR_OK && !dev) st = cuda_status(cudaEventSynchronize(ctx->host_copy_done));
   return st;
 }
 

@@ -47,6 +47,7 @@ struct vr_ctx {
   int nm[3] = {0, 0, 0};
   size_t brick_cap = 0;
   void* upload_staging = nullptr;
+  cudaEvent_t host_copy_done = nullptr;  // end of the last copy from a caller's host buffer
   size_t upload_cap = 0;
 
   // transfer function
