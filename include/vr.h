@@ -26,7 +26,12 @@
  *     and sits at world point (x, y, z) (unit spacing, §2.1 Eq. 1).
  *   - Images are H x W x 4 float32 RGBA, row-major, row 0 at the top; RGB is
  *     premultiplied over black and A = 1 - transmittance.
- *   - A context may be used from one host thread at a time.
+ *   - A context may be used from one host thread at a time, and its calls must be ordered
+ *     on the device: issue them on one stream (or order the streams yourself).  Separate
+ *     contexts on separate streams run concurrently (e.g. one frame's uploads overlapping
+ *     the previous frame's rendering).
+ *   - The first-hit surface renderer (vr_render_surface, §3.11 and §5.1) is the paper's own
+ *     renderer; vr_render is the full method of §3.10 with the transparency formula.
  */
 #ifndef VR_H
 #define VR_H
