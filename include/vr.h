@@ -49,7 +49,7 @@ typedef enum {
     VR_ERR_INVALID_ARG = 1,   /* a pointer, size or parameter is out of its range      */
     VR_ERR_OUT_OF_MEMORY = 2, /* the allocator returned NULL                           */
     VR_ERR_CUDA = 3,          /* a CUDA call failed (text via vr_last_cuda_error)      */
-    VR_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement          */
+    VR_ERR_UNSUPPORTED = 4,   /* valid request the library does not implement         */
     VR_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                    */
     VR_ERR_STATE = 6          /* call order violated (no volume / no TF / no camera,   */
                               /* or checkpoints that do not match the current state)   */
