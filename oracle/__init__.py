@@ -32,7 +32,8 @@ class Params(C.Structure):
     _fields_ = [("step", C.c_float), ("grad", C.c_int), ("ka", C.c_double), ("kd", C.c_double),
                 ("ks", C.c_double), ("shininess", C.c_double), ("light", C.c_double * 3),
                 ("headlight", C.c_int), ("ert_threshold", C.c_double),
-                ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3)]
+                ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3),
+                ("adapt_range2", C.c_double), ("adapt_range4", C.c_double)]
 
 
 class SurfaceParams(C.Structure):
@@ -118,11 +119,14 @@ def make_camera(cam: dict) -> Camera:
 
 def make_params(step=0.5, grad="central", ka=0.1, kd=0.7, ks=0.2, shininess=20.0,
                 light=(0.0, 0.0, 0.0), headlight=True, ert_threshold=0.99,
-                clip_lo=(-1e30, -1e30, -1e30), clip_hi=(1e30, 1e30, 1e30)) -> Params:
+                clip_lo=(-1e30, -1e30, -1e30), clip_hi=(1e30, 1e30, 1e30),
+                adapt_range=(-1.0, -1.0)) -> Params:
+    """adapt_range = (range bound of multiplier 2, range bound of multiplier 4), raw units;
+    negative = that level off (reading R16)."""
     g = GRAD[grad] if isinstance(grad, str) else int(grad)
     return Params(float(step), g, ka, kd, ks, shininess, (C.c_double * 3)(*light),
                   int(bool(headlight)), ert_threshold, (C.c_float * 3)(*clip_lo),
-                  (C.c_float * 3)(*clip_hi))
+                  (C.c_float * 3)(*clip_hi), float(adapt_range[0]), float(adapt_range[1]))
 
 
 def sample(ov: OracleVolume, p) -> float:

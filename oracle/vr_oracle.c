@@ -54,6 +54,14 @@
  *      ("until an alpha of 0 is hit" read as transmittance -> 0).  Output (C, 1 - T),
  *      premultiplied over black.  Shading is skipped where a == 0 (it adds nothing).
  *
+ *   R16 adaptive sampling (§5.2: coarser sampling in detail-poor regions): the regions are
+ *      the 8^3 bricks; a brick whose footprint value range max - min (raw units, FP32, the
+ *      footprint of R10) is <= adapt_range4 has multiplier m = 4, else <= adapt_range2
+ *      m = 2, else m = 1 (a negative bound disables its level).  Sample k of R4 is taken
+ *      iff k mod m(brick(p_k)) == 0, with the brick of its FP32 position (R13's FP32
+ *      position, floor >> 3, clamped to the brick grid), and stands for m samples: its
+ *      opacity is corrected to 1 - (1 - a)^m.  With every m = 1 this is R4-R9 unchanged.
+ *
  * First-hit surfaces (the renderer the paper itself implements, §3.11, with the hitpoint
  * refinement of §5.1):
  *   R13 a threshold window [lo, hi] of raw voxel values marks solid matter; the coarse
@@ -99,6 +107,7 @@ typedef struct {
     int headlight;
     double ert_threshold;
     float clip_lo[3], clip_hi[3];
+    double adapt_range2, adapt_range4; /* R16 adaptive sampling; negative = off */
 } vro_params;
 
 typedef struct {
@@ -451,10 +460,58 @@ static void eval_sample(const vro_volume *vol, const double *tf, int ntf, const 
     vro_shade(r->N, r->L, r->V, r->rgba, prm->ka, prm->kd, prm->ks, prm->shininess, r->c);
 }
 
+/* ------------------------------------------------------------ adaptive sampling (R16) */
+static int brick_count(int n) { return (n + 7) / 8; }
+
+/* Multiplier of every brick (NULL when adaptive sampling is off), from the raw value range
+ * of its footprint [8b - 1, 8b + 9] clipped to the volume. */
+static unsigned char *brick_multipliers(const vro_volume *vol, const vro_params *prm)
+{
+    if (prm->adapt_range2 < 0.0 && prm->adapt_range4 < 0.0) return NULL;
+    int nb[3] = {brick_count(vol->n[0]), brick_count(vol->n[1]), brick_count(vol->n[2])};
+    unsigned char *m = (unsigned char *)malloc((size_t)nb[0] * nb[1] * nb[2]);
+    for (int bz = 0; bz < nb[2]; ++bz)
+        for (int by = 0; by < nb[1]; ++by)
+            for (int bx = 0; bx < nb[0]; ++bx) {
+                int b[3] = {bx, by, bz}, lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = clampi(8 * b[a] - 1, 0, vol->n[a] - 1);
+                    hi[a] = clampi(8 * b[a] + 9, 0, vol->n[a] - 1);
+                }
+                double mn = INFINITY, mx = -INFINITY;
+                for (int z = lo[2]; z <= hi[2]; ++z)
+                    for (int y = lo[1]; y <= hi[1]; ++y)
+                        for (int x = lo[0]; x <= hi[0]; ++x) {
+                            double v = raw_at(vol, (long)x + (long)vol->n[0] * ((long)y + (long)vol->n[1] * z));
+                            if (v < mn) mn = v;
+                            if (v > mx) mx = v;
+                        }
+                float range = (float)mx - (float)mn;
+                int mult = 1;
+                if (prm->adapt_range4 >= 0.0 && range <= (float)prm->adapt_range4) mult = 4;
+                else if (prm->adapt_range2 >= 0.0 && range <= (float)prm->adapt_range2) mult = 2;
+                m[bx + nb[0] * (by + nb[1] * bz)] = (unsigned char)mult;
+            }
+    return m;
+}
+
+/* Multiplier of sample k of the ray (o, d, t_near): brick of its FP32 position. */
+static int sample_multiplier(const vro_volume *vol, const unsigned char *mult, const float o[3],
+                             const float d[3], float t_near, float step, int k)
+{
+    float t = fmaf((float)k + 0.5f, step, t_near);
+    int b[3];
+    for (int a = 0; a < 3; ++a) {
+        float p = fmaf(t, d[a], o[a]);
+        b[a] = clampi(((int)floorf(p)) >> 3, 0, brick_count(vol->n[a]) - 1);
+    }
+    return mult[b[0] + brick_count(vol->n[0]) * (b[1] + brick_count(vol->n[1]) * b[2])];
+}
+
 /* Render one pixel; returns the samples marched (the plain method's count). */
 static int render_pixel(const vro_volume *vol, const double *tf, int ntf, const vro_basis *b,
-                        const float lo[3], const float hi[3], const vro_params *prm, int px,
-                        int py, double out[4])
+                        const float lo[3], const float hi[3], const vro_params *prm,
+                        const unsigned char *mult, int px, int py, double out[4])
 {
     float o[3], d[3], tn;
     int K;
@@ -463,11 +520,16 @@ static int render_pixel(const vro_volume *vol, const double *tf, int ntf, const 
     double C[3] = {0, 0, 0}, T = 1.0;
     int k;
     for (k = 0; k < K; ++k) {
+        int m = 1;
+        if (mult) {
+            m = sample_multiplier(vol, mult, o, d, tn, prm->step, k);
+            if (k % m != 0) continue; /* not on this brick's coarser grid */
+        }
         double p[3], rgba[4];
         sample_point(o, d, tn, prm->step, k, p);
         double s = vro_sample(vol, p);
         vro_tf(tf, ntf, s, rgba, NULL);
-        double alpha = rgba[3];
+        double alpha = m == 1 ? rgba[3] : 1.0 - pow(1.0 - rgba[3], (double)m);
         if (alpha != 0.0) {
             double g[3], N[3], L[3], V[3], c[3], gn;
             vro_gradient(vol, prm->grad, p, g);
@@ -496,6 +558,7 @@ long long vro_render(const vro_volume *vol, const double *tf, int ntf, const vro
     render_box(prm, vol->n, lo, hi);
     long long total = 0;
     int W = cam->width;
+    unsigned char *mult = brick_multipliers(vol, prm);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
@@ -503,11 +566,12 @@ long long vro_render(const vro_volume *vol, const double *tf, int ntf, const vro
     for (int py = row0; py < row1; ++py) {
         for (int px = 0; px < W; ++px) {
             long pix = (long)py * W + px;
-            int k = render_pixel(vol, tf, ntf, &b, lo, hi, prm, px, py, out_rgba + 4 * pix);
+            int k = render_pixel(vol, tf, ntf, &b, lo, hi, prm, mult, px, py, out_rgba + 4 * pix);
             if (counts) counts[pix] = k;
             total += k;
         }
     }
+    free(mult);
     return total;
 }
 
@@ -521,15 +585,18 @@ long long vro_render_pixels(const vro_volume *vol, const double *tf, int ntf,
     camera_basis(cam, &b);
     render_box(prm, vol->n, lo, hi);
     long long total = 0;
+    unsigned char *mult = brick_multipliers(vol, prm);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
 #endif
     for (int i = 0; i < npix; ++i) {
-        int k = render_pixel(vol, tf, ntf, &b, lo, hi, prm, px[i], py[i], out_rgba + 4 * (long)i);
+        int k = render_pixel(vol, tf, ntf, &b, lo, hi, prm, mult, px[i], py[i],
+                             out_rgba + 4 * (long)i);
         if (counts) counts[i] = k;
         total += k;
     }
+    free(mult);
     return total;
 }
 
