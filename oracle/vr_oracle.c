@@ -55,12 +55,13 @@
  *      premultiplied over black.  Shading is skipped where a == 0 (it adds nothing).
  *
  *   R16 adaptive sampling (§5.2: coarser sampling in detail-poor regions): the regions are
- *      the 8^3 bricks; a brick whose footprint value range max - min (raw units, FP32, the
- *      footprint of R10) is <= adapt_range4 has multiplier m = 4, else <= adapt_range2
- *      m = 2, else m = 1 (a negative bound disables its level).  Sample k of R4 is taken
- *      iff k mod m(brick(p_k)) == 0, with the brick of its FP32 position (R13's FP32
- *      position, floor >> 3, clamped to the brick grid), and stands for m samples: its
- *      opacity is corrected to 1 - (1 - a)^m.  With every m = 1 this is R4-R9 unchanged.
+ *      32^3-voxel blocks; a region whose footprint [32r - 1, 32r + 33] (clipped to the
+ *      volume) has a value range max - min (raw units, FP32) <= adapt_range4 has multiplier
+ *      m = 4, else <= adapt_range2 m = 2, else m = 1 (a negative bound disables its level).
+ *      Sample k of R4 is taken iff k mod m(region(p_k)) == 0, with the region of its FP32
+ *      position (R13's FP32 position, floor >> 5, clamped to the region grid), and stands
+ *      for m samples: its opacity is corrected to 1 - (1 - a)^m.  With every m = 1 this is
+ *      R4-R9 unchanged.
  *
  * First-hit surfaces (the renderer the paper itself implements, §3.11, with the hitpoint
  * refinement of §5.1):
@@ -461,10 +462,11 @@ static void eval_sample(const vro_volume *vol, const double *tf, int ntf, const 
 }
 
 /* ------------------------------------------------------------ adaptive sampling (R16) */
-static int brick_count(int n) { return (n + 7) / 8; }
+enum { VRO_REGION = 32, VRO_REGION_SHIFT = 5 };
+static int brick_count(int n) { return (n + VRO_REGION - 1) / VRO_REGION; }
 
-/* Multiplier of every brick (NULL when adaptive sampling is off), from the raw value range
- * of its footprint [8b - 1, 8b + 9] clipped to the volume. */
+/* Multiplier of every region (NULL when adaptive sampling is off), from the raw value range
+ * of its footprint [32r - 1, 32r + 33] clipped to the volume. */
 static unsigned char *brick_multipliers(const vro_volume *vol, const vro_params *prm)
 {
     if (prm->adapt_range2 < 0.0 && prm->adapt_range4 < 0.0) return NULL;
@@ -475,8 +477,8 @@ static unsigned char *brick_multipliers(const vro_volume *vol, const vro_params 
             for (int bx = 0; bx < nb[0]; ++bx) {
                 int b[3] = {bx, by, bz}, lo[3], hi[3];
                 for (int a = 0; a < 3; ++a) {
-                    lo[a] = clampi(8 * b[a] - 1, 0, vol->n[a] - 1);
-                    hi[a] = clampi(8 * b[a] + 9, 0, vol->n[a] - 1);
+                    lo[a] = clampi(VRO_REGION * b[a] - 1, 0, vol->n[a] - 1);
+                    hi[a] = clampi(VRO_REGION * b[a] + VRO_REGION + 1, 0, vol->n[a] - 1);
                 }
                 double mn = INFINITY, mx = -INFINITY;
                 for (int z = lo[2]; z <= hi[2]; ++z)
@@ -495,7 +497,7 @@ static unsigned char *brick_multipliers(const vro_volume *vol, const vro_params 
     return m;
 }
 
-/* Multiplier of sample k of the ray (o, d, t_near): brick of its FP32 position. */
+/* Multiplier of sample k of the ray (o, d, t_near): region of its FP32 position. */
 static int sample_multiplier(const vro_volume *vol, const unsigned char *mult, const float o[3],
                              const float d[3], float t_near, float step, int k)
 {
@@ -503,7 +505,7 @@ static int sample_multiplier(const vro_volume *vol, const unsigned char *mult, c
     int b[3];
     for (int a = 0; a < 3; ++a) {
         float p = fmaf(t, d[a], o[a]);
-        b[a] = clampi(((int)floorf(p)) >> 3, 0, brick_count(vol->n[a]) - 1);
+        b[a] = clampi(((int)floorf(p)) >> VRO_REGION_SHIFT, 0, brick_count(vol->n[a]) - 1);
     }
     return mult[b[0] + brick_count(vol->n[0]) * (b[1] + brick_count(vol->n[1]) * b[2])];
 }
@@ -523,7 +525,7 @@ static int render_pixel(const vro_volume *vol, const double *tf, int ntf, const 
         int m = 1;
         if (mult) {
             m = sample_multiplier(vol, mult, o, d, tn, prm->step, k);
-            if (k % m != 0) continue; /* not on this brick's coarser grid */
+            if (k % m != 0) continue; /* not on this region's coarser grid */
         }
         double p[3], rgba[4];
         sample_point(o, d, tn, prm->step, k, p);
