@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--workload", choices=["ct", "ellipsoids", "sphere"], default="ct")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch", "surface"], default="main",
+    ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch", "surface", "adaptive"],
+                    default="main",
                     help="run one leg alone and print its JSON (for profiling)")
     ap.add_argument("--source-hash", choices=sorted(KERNEL_SOURCES),
                     help="print the source hash recorded beside a kernel's ncu counters")
@@ -424,6 +425,58 @@ def surface_leg(R, args):
             "mrays_per_s": H * W / (ms / 1e3) / 1e6, "rays_hit": hits}
 
 
+def adaptive_leg(R, args):
+    """Adaptive sampling (§5.2) on the CT workload: 32^3 regions whose footprint range is
+    <= 600 (raw units) take every 4th sample, <= 1500 every 2nd; the march time, the samples
+    taken and the image difference to the regular render (records cached, volume resident)."""
+    import torch
+
+    import phantoms as P
+    from paper_1609_01317_gb300 import vr
+
+    w = P.workload_ct()
+    vol = w["volume"]
+    nz, ny, nx = vol.shape
+    ctx = R.ctx
+    sh = torch.cuda.current_stream().cuda_stream or None
+    vol_dev = torch.from_numpy(vol.view(np.int16)).cuda()
+    vr.vr_upload_volume(ctx, vol_dev, "u16", nx, ny, nz, w["value_max"], sh)
+    tf_dev = torch.from_numpy(w["tf"]).cuda()
+    vr.vr_set_transfer_function(ctx, tf_dev, tf_dev.shape[0], sh)
+    cam = w["camera"]
+    vr.vr_set_camera(ctx, vr.make_camera(cam))
+    H, W = cam["height"], cam["width"]
+    kw = dict(step=w["step"], grad=w["grad"], skip_empty=True)
+    out = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for name, extra in (("regular", {}), ("adaptive", {"adapt_range": (1500.0, 600.0)})):
+        img = torch.empty((H, W, 4), device="cuda")
+        pst = vr.make_params(collect_stats=True, **kw, **extra)
+        vr.vr_render(ctx, pst, img, sh)
+        st = vr.vr_read_stats(ctx, sh)
+        p = vr.make_params(**kw, **extra)
+        for _ in range(3):
+            vr.vr_render(ctx, p, img, sh)
+        reps = max(10, min(args.steps, 100))
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps)]
+        for i in range(reps):
+            flush.fill_(float(i))
+            ev[i][0].record()
+            vr.vr_render(ctx, p, img, sh)
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        out[name] = (statistics.mean(a.elapsed_time(b) for a, b in ev), st, img)
+    diff = (out["adaptive"][2] - out["regular"][2]).abs().amax(dim=-1)
+    return {"workload": "ct512x512x361_u16_persp1920x1080_zh_adaptive",
+            "adapt_range": {"m2": 1500.0, "m4": 600.0},
+            "regular_ms": out["regular"][0], "adaptive_ms": out["adaptive"][0],
+            "speedup": out["regular"][0] / out["adaptive"][0],
+            "samples_taken": out["adaptive"][1]["samples_visited"],
+            "samples_taken_regular": out["regular"][1]["samples_visited"],
+            "image_max_abs_diff": float(diff.max().item()),
+            "image_mean_abs_diff": float(diff.mean().item())}
+
+
 def fwd_bwd_leg(R, args):
     """Differentiable workload: 128^3 float32 blurred density, learnable 256-entry TF,
     16 views at 256x256, central differences, step 0.5.  Times the forward that records
@@ -616,6 +669,7 @@ def run_ours(args):
     if not args.no_extras:
         line["fwd_bwd"] = fwd_bwd_leg(R, args)
         line["surface"] = surface_leg(R, args)
+        line["adaptive"] = adaptive_leg(R, args)
         line["batch"] = batch_leg(args)
     if not args.no_extras and world == 1:
         # end to end through the C ABI with host buffers: H2D of the volume and TF, D2H of
@@ -703,9 +757,10 @@ def run_leg(args):
 
     build.build()
     torch.cuda.set_device(0)
-    if args.leg in ("fwd_bwd", "surface"):
+    if args.leg in ("fwd_bwd", "surface", "adaptive"):
         R = Renderer(0)
-        out = (fwd_bwd_leg if args.leg == "fwd_bwd" else surface_leg)(R, args)
+        out = {"fwd_bwd": fwd_bwd_leg, "surface": surface_leg,
+               "adaptive": adaptive_leg}[args.leg](R, args)
         R.close()
     else:
         out = batch_leg(args)

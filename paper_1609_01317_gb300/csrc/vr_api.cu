@@ -132,6 +132,7 @@ RenderDev render_dev_for(const int n[3], float value_max, const vr_render_params
   r.sh.shininess = p->shininess;
   for (int a = 0; a < 3; ++a) r.sh.light[a] = p->light[a];
   r.sh.headlight = p->headlight ? 1 : 0;
+  r.mult = nullptr;
   return r;
 }
 
@@ -202,6 +203,8 @@ vr_status check_params(const vr_render_params* p) {
   if (!finite3(p->light)) return VR_ERR_INVALID_ARG;
   for (int a = 0; a < 3; ++a)
     if (std::isnan(p->clip_lo[a]) || std::isnan(p->clip_hi[a])) return VR_ERR_INVALID_ARG;
+  if (p->adaptive && (std::isnan(p->adapt_range2) || std::isnan(p->adapt_range4)))
+    return VR_ERR_INVALID_ARG;
   return VR_OK;
 }
 
@@ -274,6 +277,17 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
     vr_status st = cuda_status(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
     if (st != VR_OK) return st;
     L.stats = ctx->stats;
+  }
+  if (p->adaptive) {
+    // sampling multiplier of every macro brick from its footprint's value range (§5.2)
+    const int nmacro = ctx->nm[0] * ctx->nm[1] * ctx->nm[2];
+    vr_status st = ensure(ctx, &ctx->adapt_mult, &ctx->adapt_mult_cap, (size_t)nmacro);
+    if (st != VR_OK) return st;
+    st = cuda_status(launch_macro_multiplier(ctx->brick_minmax, ctx->nb, ctx->nm, p->adapt_range2,
+                                             p->adapt_range4,
+                                             static_cast<uint8_t*>(ctx->adapt_mult), s));
+    if (st != VR_OK) return st;
+    L.r.mult = static_cast<const uint8_t*>(ctx->adapt_mult);
   }
   const vr_status st = cuda_status(launch_march(L, s));
   if (st == VR_OK) ctx->stats_valid = ctx->stats_valid || p->collect_stats;
@@ -358,6 +372,7 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->tf_partial);
   ctx_free(ctx, ctx->batch_tab);
   ctx_free(ctx, ctx->surf_vis);
+  ctx_free(ctx, ctx->adapt_mult);
   ctx_free(ctx, ctx->rec);
   delete ctx;
 }
@@ -519,6 +534,7 @@ vr_status vr_checkpoint_bytes(vr_ctx* ctx, const vr_render_params* params, size_
   if (!ctx || !bytes) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
+  if (params->adaptive) return VR_ERR_UNSUPPORTED;  // the adjoint marches the regular grid
   if (!ctx->has_volume || !ctx->has_camera) return VR_ERR_STATE;
   int nrays, nslots;
   ckpt_layout(ctx, params, &nrays, &nslots, bytes);
@@ -530,6 +546,7 @@ vr_status vr_render_forward_train(vr_ctx* ctx, const vr_render_params* params, f
   if (!ctx || !out_rgba || !checkpoints) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
+  if (params->adaptive) return VR_ERR_UNSUPPORTED;  // the adjoint marches the regular grid
   if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
   if (((uintptr_t)checkpoints & 255) != 0) return VR_ERR_INVALID_ARG;
   int nrays, nslots;
@@ -573,6 +590,7 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
   if (!ctx || nviews < 1 || !cams || !checkpoints || !grad_rgba) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
+  if (params->adaptive) return VR_ERR_UNSUPPORTED;  // the adjoint marches the regular grid
   if (!ctx->has_volume || !ctx->has_tf) return VR_ERR_STATE;
   // validate every view before queuing any work
   const CkptRecord* recs[256];

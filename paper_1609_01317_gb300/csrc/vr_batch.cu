@@ -181,7 +181,7 @@ vr_status vr_batch_create(vr_batch** out, vr_ctx* const* ctxs, int nctx, const v
   if (!ctxs || nctx < 1 || !cams || !ctx_of_cam || ncams < 1 || !outs) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
-  if (params->collect_stats) return VR_ERR_UNSUPPORTED;
+  if (params->collect_stats || params->adaptive) return VR_ERR_UNSUPPORTED;
   for (int i = 0; i < nctx; ++i) {
     if (!ctxs[i]) return VR_ERR_INVALID_ARG;
     if (!ctxs[i]->has_volume || !ctxs[i]->has_tf) return VR_ERR_STATE;
@@ -340,7 +340,7 @@ vr_status vr_render_batch(vr_ctx* const* vols, const vr_camera* cams, const int*
   if (!vols || !cams || !vol_of_cam || n < 1 || !outs) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
-  if (params->collect_stats) return VR_ERR_UNSUPPORTED;
+  if (params->collect_stats || params->adaptive) return VR_ERR_UNSUPPORTED;
   int nvol = 0;
   for (int i = 0; i < n; ++i) {
     if (vol_of_cam[i] < 0 || !outs[i]) return VR_ERR_INVALID_ARG;

@@ -71,6 +71,7 @@ struct RenderDev {
   float lo[3], hi[3]; // sampling box: clip box intersected with [0, n-1]^3
   float gscale;       // gradient operator scale / value_max
   ShadeDev sh;
+  const uint8_t* mult;  // per-macro-brick sampling multiplier (adaptive sampling, §5.2), or null
 };
 
 // ----------------------------------------------------------------------- voxel fetch
@@ -425,6 +426,11 @@ __device__ __forceinline__ void shade(const ShadeDev& sh, const CamDev& cam, con
   r.c[0] = fmaf(rgba.x, k, sh.ks * spec);
   r.c[1] = fmaf(rgba.y, k, sh.ks * spec);
   r.c[2] = fmaf(rgba.z, k, sh.ks * spec);
+}
+
+// Index of the macro brick holding brick b.
+__device__ __forceinline__ int macro_of(const VolDev& V, const int b[3]) {
+  return (b[0] >> kMacroShift) + V.nm[0] * ((b[1] >> kMacroShift) + V.nm[1] * (b[2] >> kMacroShift));
 }
 
 // Index of the brick containing p (clamped to the brick grid).

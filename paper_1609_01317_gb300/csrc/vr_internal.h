@@ -79,6 +79,10 @@ struct vr_ctx {
   float* tf_partial = nullptr;
   size_t tf_partial_cap = 0;
 
+  // per-macro-brick sampling multipliers of an adaptive render
+  void* adapt_mult = nullptr;
+  size_t adapt_mult_cap = 0;
+
   // brick and macro-brick visibility for a surface render's threshold window
   void* surf_vis = nullptr;
   size_t surf_vis_cap = 0;
@@ -133,6 +137,10 @@ cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t 
 cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
                                     int ntf, float scale, uint8_t* vis, int* list,
                                     uint8_t* mvis, const int nm[3], cudaStream_t s);
+// mult[m] = 4 if the footprint range max - min of macro brick m is <= r4 (r4 >= 0), else 2
+// if <= r2 (r2 >= 0), else 1
+cudaError_t launch_macro_multiplier(const float2* mm, const int nb[3], const int nm[3], float r2,
+                                    float r4, uint8_t* mult, cudaStream_t s);
 // records of the bricks in `list` (as built by launch_brick_visibility, `need` its vis
 // array), or of every brick when `list` is null
 cudaError_t launch_records(const VolDev& V, int dtype, int op, const uint8_t* need,

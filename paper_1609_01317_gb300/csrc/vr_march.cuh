@@ -57,11 +57,18 @@ __device__ __forceinline__ void corners_gradient(const Corners& k, const Cell& c
 // between lies in one of those bricks (each lane's interval starts at its own sample and the
 // starts are consecutive), so nothing visible is skipped.
 // TFS: the transfer function is read from s_tf, a copy in shared memory.
-template <bool CKPT, bool TFS = false>
+// ADAPT: adaptive sampling (§5.2): sample k is taken iff k mod m == 0, m in {1, 2, 4} the
+// multiplier of its macro brick (L.r.mult), with opacity 1 - (1 - a)^m.  A group whose span of
+// 4 m samples lies in one macro brick of multiplier m (its first and last samples share it;
+// the macro index is monotone along the ray) takes samples k, k + m, k + 2m, k + 3m; any
+// other group takes the next 1-4 consecutive samples up to a multiple of 4 (so the following
+// group starts aligned to every multiplier) and drops the samples off their region's grid.
+template <bool CKPT, bool TFS = false, bool ADAPT = false>
 __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, bool active,
                                           int q, unsigned qmask, unsigned& hit, unsigned& plain,
                                           unsigned& visited, unsigned& shaded,
                                           const float4* s_tf = nullptr) {
+  static_assert(!(CKPT && ADAPT), "the adjoint's checkpoints follow the regular grid");
   const int W = L.cam.width, H = L.cam.height;
   const int ray = py * W + px;
   const int qbase = (threadIdx.x & 31) & ~3;
@@ -76,14 +83,47 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
 #pragma unroll
   for (int a = 0; a < 3; ++a) inv_d[a] = d[a] != 0.0f ? 1.0f / d[a] : 0.0f;
   while (k < K) {
-    const int ks = k + q;
-    const bool live = ks < K;
+    int stride = 1, span = 4;  // samples between the quad's lanes; samples the group covers
+    if constexpr (ADAPT) {
+      float p0[3];
+      const float t0 = fmaf((float)k + 0.5f, step, tn);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) p0[a] = fmaf(t0, d[a], o[a]);
+      int b0[3];
+      brick_of(L.V, p0, b0);
+      const int mi0 = macro_of(L.V, b0);
+      const int m0 = __ldg(L.r.mult + mi0);
+      if (m0 > 1 && (k & (m0 - 1)) == 0) {
+        const int kl = min(k + 4 * m0 - 1, K - 1);
+        float pl[3];
+        const float tl = fmaf((float)kl + 0.5f, step, tn);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) pl[a] = fmaf(tl, d[a], o[a]);
+        int bl[3];
+        brick_of(L.V, pl, bl);
+        if (macro_of(L.V, bl) == mi0) {
+          stride = m0;
+          span = 4 * m0;
+        }
+      }
+      if (stride == 1) span = 4 - (k & 3);
+    }
+    const int ks = k + q * stride;
+    const bool live = q * stride < span && ks < K;
     float p[3];
     const float t = fmaf((float)ks + 0.5f, step, tn);
 #pragma unroll
     for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
     bool vis = live;
-    int kn = K;
+    int kn = ks < K ? k + span : K;  // a lane past the group's span bounds the jump by it
+    int w = stride;                  // samples this lane's sample stands for
+    if constexpr (ADAPT) {
+      if (live && stride == 1) {
+        int bm[3];
+        brick_of(L.V, p, bm);
+        w = __ldg(L.r.mult + macro_of(L.V, bm));
+      }
+    }
     if (L.r.skip && live) {
       int b[3];
       const int bi = brick_of(L.V, p, b);
@@ -104,6 +144,7 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
         if (kn <= ks) kn = ks + 1;
       }
     }
+    // a live lane in a visible brick keeps the group; otherwise the group jumps
     if (((__ballot_sync(qmask, vis) >> qbase) & 0xFu) == 0u) {
       // the whole group lies in empty bricks: jump
       kn = max(kn, __shfl_xor_sync(qmask, kn, 1));
@@ -117,6 +158,9 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
       continue;
     }
     float alpha = 0.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+    if constexpr (ADAPT) {
+      if (stride == 1 && (ks & (w - 1)) != 0) vis = false;  // off its brick's coarser grid
+    }
     if (vis) {
       ++visited;
       const Cell c = cell_of(L.V, p);
@@ -125,6 +169,12 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
       const float s = corners_value(cr, c);
       const TfSample ts = tf_lookup<TFS>(L.tf, s, s_tf);
       alpha = ts.rgba.w;
+      if constexpr (ADAPT) {
+        if (w > 1) {  // the sample stands for w samples: 1 - (1 - a)^w, w in {2, 4}
+          const float om = 1.0f - alpha, om2 = om * om;
+          alpha = 1.0f - (w == 2 ? om2 : om2 * om2);
+        }
+      }
       if (alpha != 0.0f) {
         ++shaded;
         float g[3];
@@ -152,7 +202,7 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
     int used = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      if (!stop && k + j < K) {
+      if (!stop && j * stride < span && k + j * stride < K) {
         if (CKPT && q == 0 && k + j > 0 && ((k + j) & (kCkptStride - 1)) == 0)
           L.ck_T[(size_t)(((k + j) >> 5) - 1) * (W * H) + ray] = T;
         const float aj = a4[j];
@@ -163,11 +213,11 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
           C2 = fmaf(ta, c4[j][2], C2);
           T = T * (1.0f - aj);
         }
-        used = j + 1;
+        used = j * stride + 1;
         if (1.0f - T >= L.r.ert) stop = true;
       }
     }
-    k += used;
+    k += stop ? used : span;
     if (stop) break;
   }
   const int kend = k < K ? k : K;

@@ -222,7 +222,7 @@ extern "C" vr_status vr_render_noalloc(const void* voxels, vr_dtype dtype, int n
   if (ntf < 2 || ntf > kNoAllocMaxTf) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
-  if (params->collect_stats) return VR_ERR_UNSUPPORTED;
+  if (params->collect_stats || params->adaptive) return VR_ERR_UNSUPPORTED;
   CamDev basis;
   st = check_camera(cam, &basis);
   if (st != VR_OK) return st;

@@ -21,7 +21,8 @@ constexpr int kTileW = 4, kTileH = 2;  // one warp's pixels (a quad of lanes per
 constexpr int kMaxSharedTf = 1024;  // tables up to this many entries are copied to shared memory
 
 // TFS: the block copies the transfer function (n <= kMaxSharedTf entries) to shared memory.
-template <bool CKPT, bool TFS>
+// ADAPT: adaptive sampling with the per-brick multipliers L.r.mult.
+template <bool CKPT, bool TFS, bool ADAPT = false>
 __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
   extern __shared__ float4 s_tf[];
   if constexpr (TFS) {
@@ -42,7 +43,8 @@ __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
     if (tile >= tiles) break;
     const int px = (tile % tiles_x) * kTileW + (qd & 3);
     const int py = (tile / tiles_x) * kTileH + (qd >> 2);
-    march_ray<CKPT, TFS>(L, px, py, px < W && py < H, q, qmask, hit, plain, visited, shaded, s_tf);
+    march_ray<CKPT, TFS, ADAPT>(L, px, py, px < W && py < H, q, qmask, hit, plain, visited,
+                                shaded, s_tf);
     __syncwarp();
   }
   if (L.stats) {
@@ -60,22 +62,22 @@ __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
 }
 
 // Blocks that keep every SM busy once (the kernel is persistent).
-template <bool CKPT, bool TFS>
+template <bool CKPT, bool TFS, bool ADAPT>
 static int persistent_blocks(size_t smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march<CKPT, TFS>, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march<CKPT, TFS, ADAPT>, kThreads, smem);
   return (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
 }
 
-template <bool CKPT>
+template <bool CKPT, bool ADAPT>
 static void launch_march_k(const MarchLaunch& L, cudaStream_t s) {
   if (L.tf.n <= kMaxSharedTf) {
     const size_t smem = sizeof(float4) * (size_t)L.tf.n;
-    k_march<CKPT, true><<<persistent_blocks<CKPT, true>(smem), kThreads, smem, s>>>(L);
+    k_march<CKPT, true, ADAPT><<<persistent_blocks<CKPT, true, ADAPT>(smem), kThreads, smem, s>>>(L);
   } else {
-    k_march<CKPT, false><<<persistent_blocks<CKPT, false>(0), kThreads, 0, s>>>(L);
+    k_march<CKPT, false, ADAPT><<<persistent_blocks<CKPT, false, ADAPT>(0), kThreads, 0, s>>>(L);
   }
 }
 
@@ -83,8 +85,9 @@ cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s) {
   // the tile counter starts at zero for every launch
   cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  if (L.ck_kend) launch_march_k<true>(L, s);
-  else launch_march_k<false>(L, s);
+  if (L.ck_kend) launch_march_k<true, false>(L, s);
+  else if (L.r.mult) launch_march_k<false, true>(L, s);
+  else launch_march_k<false, false>(L, s);
   return cudaGetLastError();
 }
 

@@ -261,6 +261,39 @@ cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------ adaptive-sampling multipliers
+// §5.2: detail-poor regions are sampled more coarsely.  The regions are the macro bricks
+// (4 x 4 x 4 bricks, 32^3 voxels); a macro brick's footprint [32m - 1, 32m + 33] is the union
+// of its bricks' footprints, so its value range comes from their min / max.
+__global__ void k_macro_multiplier(const float2* __restrict__ mm, int nbx, int nby, int nbz,
+                                   int nmx, int nmy, int nmz, float r2, float r4,
+                                   uint8_t* __restrict__ mult) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nmx * nmy * nmz) return;
+  const int mx = i % nmx, my = (i / nmx) % nmy, mz = i / (nmx * nmy);
+  float lo = __int_as_float(0x7f800000), hi = -lo;
+  for (int z = mz << kMacroShift; z < min((mz + 1) << kMacroShift, nbz); ++z)
+    for (int y = my << kMacroShift; y < min((my + 1) << kMacroShift, nby); ++y)
+      for (int x = mx << kMacroShift; x < min((mx + 1) << kMacroShift, nbx); ++x) {
+        const float2 m = mm[x + nbx * (y + nby * z)];
+        lo = fminf(lo, m.x);
+        hi = fmaxf(hi, m.y);
+      }
+  const float range = hi - lo;
+  uint8_t k = 1;
+  if (r4 >= 0.0f && range <= r4) k = 4;
+  else if (r2 >= 0.0f && range <= r2) k = 2;
+  mult[i] = k;
+}
+
+cudaError_t launch_macro_multiplier(const float2* mm, const int nb[3], const int nm[3], float r2,
+                                    float r4, uint8_t* mult, cudaStream_t s) {
+  const int n = nm[0] * nm[1] * nm[2];
+  k_macro_multiplier<<<(n + 127) / 128, 128, 0, s>>>(mm, nb[0], nb[1], nb[2], nm[0], nm[1], nm[2],
+                                                     r2, r4, mult);
+  return cudaGetLastError();
+}
+
 }  // namespace vr
 
 namespace vr {
