@@ -96,10 +96,11 @@ typedef struct {
     float clip_hi[3];
     int collect_stats;   /* 1: count rays and samples (read with vr_read_stats)         */
     /* Adaptive sampling (§5.2: coarser sampling in detail-poor regions), 0 = off.  With it
-     * on, each 8^3 brick gets a multiplier m: 4 if its footprint's raw value range
-     * (max - min) is <= adapt_range4, else 2 if <= adapt_range2, else 1 (a negative bound
-     * disables its level); sample k is taken iff k mod m(brick of sample k) == 0 and its
-     * opacity is corrected to 1 - (1 - a)^m (it stands for m samples).  Only vr_render
+     * on, each 32^3-voxel region gets a multiplier m: 4 if the raw value range (max - min)
+     * of its footprint [32r - 1, 32r + 33] is <= adapt_range4, else 2 if <= adapt_range2,
+     * else 1 (a negative bound disables its level); sample k is taken iff
+     * k mod m(region of sample k) == 0 and its opacity is corrected to 1 - (1 - a)^m (it
+     * stands for m samples).  Only vr_render
      * supports it (VR_ERR_UNSUPPORTED elsewhere).  The sample counters still count every
      * sample of the regular grid up to termination (rays_hit, samples_plain) and the
      * samples taken (samples_visited). */
