@@ -309,9 +309,9 @@ namespace vr {
 // A brick needs the records of voxels [8b, 8b+8]^3 (its cells' corners); with skipping
 // on, only visible bricks are visited.  Each voxel is written by the brick whose core
 // [8b, 8b+8)^3 holds it when that brick is computed, else by the computed brick whose
-// upper face it lies on (several such bricks write the same value).  Persistent blocks take
-// bricks in grid stride: the 11^3 clamp-to-edge neighbourhood [8b-1, 8b+9]^3 is staged in
-// shared memory, then 81 threads each stream one (x, y) column of records along z.
+// upper face it lies on (several such bricks write the same value).  Per brick the 11^3
+// clamp-to-edge neighbourhood [8b-1, 8b+9]^3 is staged in shared memory, then the (x, y)
+// columns of records are streamed along z (see k_records).
 // Sums of one z plane of a voxel's 3x3x3 neighbourhood (pl[y][x], the voxel at [w+1][u+1])
 // from which the operators of §3.5 are assembled.  Every 3x3x3 operator here weights a tap
 // by its class only: centre w0, edge w1, corner w2 of the 3x3 mask across the component's
@@ -352,75 +352,133 @@ __device__ __forceinline__ PlaneSums plane_sums(const float (*pl)[12], int u, in
   return r;
 }
 
+// Plane sums of two neighbouring voxels (tile columns u + 1 and u + 2, rows w .. w + 2) from
+// one 3 x 4 patch read with 64-bit shared loads (u even); the two voxels share the patch's
+// column differences and sums along y.
+template <int OP>
+__device__ __forceinline__ void plane_sums2(const float (*pl)[12], int u, int w, PlaneSums& A,
+                                            PlaneSums& B) {
+  float p[3][4];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const float2 lo = *reinterpret_cast<const float2*>(&pl[w + b][u]);
+    const float2 hi = *reinterpret_cast<const float2*>(&pl[w + b][u + 2]);
+    p[b][0] = lo.x;
+    p[b][1] = lo.y;
+    p[b][2] = hi.x;
+    p[b][3] = hi.y;
+  }
+  A.ax = p[1][2] - p[1][0];
+  B.ax = p[1][3] - p[1][1];
+  A.c = p[1][1];
+  B.c = p[1][2];
+  if constexpr (OP == OP_CENTRAL) {
+    A.ay = p[2][1] - p[0][1];
+    B.ay = p[2][2] - p[0][2];
+    A.bx = A.by = A.q = B.bx = B.by = B.q = 0.0f;
+  } else {
+    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+    float dy[4], sy[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      dy[c] = p[2][c] - p[0][c];
+      sy[c] = p[0][c] + p[2][c];
+    }
+    A.bx = sy[2] - sy[0];
+    B.bx = sy[3] - sy[1];
+    A.ay = dy[1];
+    B.ay = dy[2];
+    A.by = dy[0] + dy[2];
+    B.by = dy[1] + dy[3];
+    A.q = fmaf(w0, p[1][1], fmaf(w1, sy[1] + (p[1][0] + p[1][2]), w2 * (sy[0] + sy[2])));
+    B.q = fmaf(w0, p[1][2], fmaf(w1, sy[2] + (p[1][1] + p[1][3]), w2 * (sy[1] + sy[3])));
+  }
+}
+
+// The record of a voxel from the plane sums below, at and above it.
+template <int OP>
+__device__ __forceinline__ float4 record_of(const PlaneSums& lo, const PlaneSums& md,
+                                            const PlaneSums& hi) {
+  if constexpr (OP == OP_CENTRAL) {
+    return make_float4(md.ax, md.ay, hi.c - lo.c, md.c);
+  } else {
+    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
+    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
+    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
+    return make_float4(fmaf(w0, md.ax, fmaf(w1, md.bx + (lo.ax + hi.ax), w2 * (lo.bx + hi.bx))),
+                       fmaf(w0, md.ay, fmaf(w1, md.by + (lo.ay + hi.ay), w2 * (lo.by + hi.by))),
+                       hi.q - lo.q, md.c);
+  }
+}
+
+// Stage padded row (y0 - 1 + j, z0 - 1 + k) of brick (x0, y0, z0) from padded x = x0, i.e.
+// voxels x0 - 1 .. x0 + 14, into tile[k][j][0..11]: one aligned 16-element vector (row
+// pitches are multiples of 16 elements and x0 of 8; the vector ends inside the row); rows
+// beyond n are clamped to n (inside the padded border, where E is the edge value).
+template <int VTYPE>
+__device__ __forceinline__ void stage_row(float (*tile)[11][12], const VolDev& V, int x0, int y0,
+                                          int z0, int j, int k) {
+  using T = typename VoxelT<VTYPE>::T;
+  const int Y = min(y0 - 1 + j, V.n[1]), Z = min(z0 - 1 + k, V.n[2]);
+  const T* row = static_cast<const T*>(V.data) + (size_t)V.px * (Y + kPadLo) +
+                 (size_t)V.pxy * (Z + kPadLo) + x0;
+  float e[16];
+  if constexpr (VTYPE == VT_U8) {
+    const uint2 a0 = __ldg(reinterpret_cast<const uint2*>(row));
+    const uint2 a1 = __ldg(reinterpret_cast<const uint2*>(row) + 1);
+    const unsigned wv[4] = {a0.x, a0.y, a1.x, a1.y};
+#pragma unroll
+    for (int i = 0; i < 16; ++i) e[i] = (float)((wv[i >> 2] >> (8 * (i & 3))) & 0xffu);
+  } else {
+    load16<VTYPE>(row, e);
+  }
+  float4* dst = reinterpret_cast<float4*>(&tile[k][j][0]);
+  dst[0] = make_float4(e[0], e[1], e[2], e[3]);
+  dst[1] = make_float4(e[4], e[5], e[6], e[7]);
+  dst[2] = make_float4(e[8], e[9], e[10], e[11]);
+}
+
+// Persistent blocks of 64 threads take bricks in grid stride (from `list` when given).  Work
+// items: 32 threads for the 8 x 8 core columns as pairs (x offsets 2p, 2p + 1), 4 for the
+// pairs of the upper y face (row 8) and 9 for the upper x face column (x offset 8, rows
+// 0..8); each streams its column(s) along z with rolling plane sums.
 template <int VTYPE, int OP>
-__global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* __restrict__ need,
-                                                 const int* __restrict__ list,
-                                                 float4* __restrict__ rec) {
+__global__ void __launch_bounds__(64) k_records(const VolDev V, const uint8_t* __restrict__ need,
+                                                const int* __restrict__ list,
+                                                float4* __restrict__ rec) {
   __shared__ __align__(16) float tile[11][11][12];  // [z][y][x], x padded to 12
   const int t = threadIdx.x;
   const int nbx = V.nb[0], nby = V.nb[1];
   const int nbricks = nbx * nby * V.nb[2];
   const int nx = V.n[0], ny = V.n[1], nz = V.n[2];
-  const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
-  const int u = t % 9, w = t / 9;  // x, y offsets in the brick (threads below 81)
+  int u = 0, w = 0, ncol = 0;  // first column, row, columns of this thread (0: idle)
+  if (t < 32) {
+    u = 2 * (t & 3);
+    w = t >> 2;
+    ncol = 2;
+  } else if (t < 36) {
+    u = 2 * (t - 32);
+    w = kBrick;
+    ncol = 2;
+  } else if (t < 45) {
+    u = kBrick;
+    w = t - 36;
+    ncol = 1;
+  }
   const int nwork = list ? list[0] : nbricks;
-  using T = typename VoxelT<VTYPE>::T;
-  // stage: thread (j, k) < 121 loads padded row (y0-1+j, z0-1+k) from padded x = x0, i.e.
-  // voxels x0-1 .. x0+14, as one aligned 16-element vector (row pitches are multiples of
-  // 16 elements and x0 of 8; the vector ends inside the row); rows beyond n are clamped to
-  // n (still inside the padded border, where E is the edge value).  The next brick's rows
-  // are loaded into registers while the current one is computed.
-  constexpr int kWords = 16 * (int)sizeof(T) / 4;
-  const int sj = t % 11, sk = t / 11;
-  uint32_t raw[kWords];
-  auto load_row = [&](int item) {
-    const int b = list ? list[1 + item] : item;
-    const int Y = min((((b / nbx) % nby) << kBrickShift) - 1 + sj, ny);
-    const int Z = min(((b / (nbx * nby)) << kBrickShift) - 1 + sk, nz);
-    const T* row = v + (size_t)V.px * (Y + kPadLo) + (size_t)V.pxy * (Z + kPadLo) +
-                   ((b % nbx) << kBrickShift);
-    if constexpr (sizeof(T) == 1) {
-      const uint2 a0 = __ldg(reinterpret_cast<const uint2*>(row));
-      const uint2 a1 = __ldg(reinterpret_cast<const uint2*>(row) + 1);
-      raw[0] = a0.x; raw[1] = a0.y; raw[2] = a1.x; raw[3] = a1.y;
-    } else {
-#pragma unroll
-      for (int q = 0; q < kWords / 4; ++q) {
-        const uint4 a = __ldg(reinterpret_cast<const uint4*>(row) + q);
-        raw[4 * q] = a.x; raw[4 * q + 1] = a.y; raw[4 * q + 2] = a.z; raw[4 * q + 3] = a.w;
-      }
-    }
-  };
-  if (t < 121 && (int)blockIdx.x < nwork) load_row(blockIdx.x);
+  const size_t zstride = (size_t)nx * ny;
   for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
     const int bid = list ? list[1 + item] : item;
     const int bx = bid % nbx, by = (bid / nbx) % nby, bz = bid / (nbx * nby);
     const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
-    if (t < 121) {
-      float e[12];
-#pragma unroll
-      for (int i = 0; i < 12; ++i) {
-        if constexpr (sizeof(T) == 1) {
-          e[i] = (float)((raw[i >> 2] >> (8 * (i & 3))) & 0xffu);
-        } else if constexpr (sizeof(T) == 2) {
-          const unsigned short h = (unsigned short)((raw[i >> 1] >> (16 * (i & 1))) & 0xffffu);
-          if constexpr (VTYPE == VT_F16) e[i] = __half2float(__ushort_as_half(h));
-          else e[i] = (float)h;
-        } else {
-          e[i] = __uint_as_float(raw[i]);
-        }
-      }
-      float4* dst = reinterpret_cast<float4*>(&tile[sk][sj][0]);
-      dst[0] = make_float4(e[0], e[1], e[2], e[3]);
-      dst[1] = make_float4(e[4], e[5], e[6], e[7]);
-      dst[2] = make_float4(e[8], e[9], e[10], e[11]);
-      if (item + (int)gridDim.x < nwork) load_row(item + gridDim.x);
-    }
+    for (int r = t; r < 121; r += 64) stage_row<VTYPE>(tile, V, x0, y0, z0, r % 11, r / 11);
     __syncthreads();
     const int x = x0 + u, y = y0 + w;
-    if (t < 81 && x < nx && y < ny) {
-      // which of this column's records to write: the core always; a face voxel when the
-      // brick that owns it is not computed
+    if (ncol && x < nx && y < ny) {
+      // which of this item's records to write: the core always; a face voxel when the brick
+      // that owns it is not computed
       const int ox = u == kBrick, oy = w == kBrick;
       bool wr_lo = true, wr_top = false;
       if (need) {
@@ -431,35 +489,34 @@ __global__ void __launch_bounds__(128) k_records(const VolDev V, const uint8_t* 
       }
       const int qn = min(kBrick + 1, nz - z0);
       float4* out = rec + (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z0);
-      const size_t zstride = (size_t)nx * ny;
       if (wr_lo || (wr_top && qn > kBrick)) {
-        // per-plane sums of the 3x3 (x, y) neighbourhood; plane k is voxel z0 - 1 + k
-        PlaneSums ps[3];
-        ps[0] = plane_sums<OP>(tile[0], u, w);
-        ps[1] = plane_sums<OP>(tile[1], u, w);
+        if (ncol == 2) {
+          const bool two = x + 1 < nx;
+          PlaneSums A[3], B[3];
+          plane_sums2<OP>(tile[0], u, w, A[0], B[0]);
+          plane_sums2<OP>(tile[1], u, w, A[1], B[1]);
 #pragma unroll
-        for (int q = 0; q <= kBrick; ++q) {
-          if (q < qn && (q < kBrick ? wr_lo : wr_top)) {
-            ps[(q + 2) % 3] = plane_sums<OP>(tile[q + 2], u, w);
-            const PlaneSums& lo = ps[q % 3];
-            const PlaneSums& md = ps[(q + 1) % 3];
-            const PlaneSums& hi = ps[(q + 2) % 3];
-            float g[3];
-            if constexpr (OP == OP_CENTRAL) {
-              g[0] = md.ax;
-              g[1] = md.ay;
-              g[2] = hi.c - lo.c;
-            } else {
-              constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
-              constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
-              constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
-              g[0] = fmaf(w0, md.ax, fmaf(w1, md.bx + (lo.ax + hi.ax), w2 * (lo.bx + hi.bx)));
-              g[1] = fmaf(w0, md.ay, fmaf(w1, md.by + (lo.ay + hi.ay), w2 * (lo.by + hi.by)));
-              g[2] = hi.q - lo.q;
+          for (int q = 0; q <= kBrick; ++q) {
+            if (q < qn) {
+              plane_sums2<OP>(tile[q + 2], u, w, A[(q + 2) % 3], B[(q + 2) % 3]);
+              if (q < kBrick ? wr_lo : wr_top) {
+                out[q * zstride] = record_of<OP>(A[q % 3], A[(q + 1) % 3], A[(q + 2) % 3]);
+                if (two)
+                  out[q * zstride + 1] = record_of<OP>(B[q % 3], B[(q + 1) % 3], B[(q + 2) % 3]);
+              }
             }
-            out[q * zstride] = make_float4(g[0], g[1], g[2], md.c);
-          } else if (q < qn) {
-            ps[(q + 2) % 3] = plane_sums<OP>(tile[q + 2], u, w);
+          }
+        } else {
+          PlaneSums ps[3];
+          ps[0] = plane_sums<OP>(tile[0], u, w);
+          ps[1] = plane_sums<OP>(tile[1], u, w);
+#pragma unroll
+          for (int q = 0; q <= kBrick; ++q) {
+            if (q < qn) {
+              ps[(q + 2) % 3] = plane_sums<OP>(tile[q + 2], u, w);
+              if (q < kBrick ? wr_lo : wr_top)
+                out[q * zstride] = record_of<OP>(ps[q % 3], ps[(q + 1) % 3], ps[(q + 2) % 3]);
+            }
           }
         }
       }
@@ -476,11 +533,11 @@ static void launch_records_k(const VolDev& V, const uint8_t* need, const int* li
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_records<VTYPE, OP>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_records<VTYPE, OP>, 64, 0);
     grid = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
   }
   const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
-  k_records<VTYPE, OP><<<min(grid, nbricks), 128, 0, s>>>(V, need, list, rec);
+  k_records<VTYPE, OP><<<min(grid, nbricks), 64, 0, s>>>(V, need, list, rec);
 }
 
 template <int VTYPE>
