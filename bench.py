@@ -278,6 +278,17 @@ def oracle_sample(w, seconds):
             "cores": oracle.num_threads()}
 
 
+def bench_config(w, world):
+    """The workload description shared by both arms' JSON lines."""
+    nz, ny, nx = w["volume"].shape
+    cam = w["camera"]
+    return {"workload": w["name"], "volume": f"{nx}x{ny}x{nz} {dtype_name(w['volume'])}",
+            "image": f"{cam['width']}x{cam['height']}", "grad": w["grad"], "step": w["step"],
+            "skip_empty": w["skip_empty"], "ert": 0.99,
+            "l2": "flushed between steps (256 MiB write); volume 189 MB > L2",
+            "parallelism": f"replicas{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -300,8 +311,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * secs / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["name"], "image": f"{cam['width']}x{cam['height']}",
-                   "grad": w["grad"], "step": w["step"]},
+        "config": bench_config(w, args.gpus),
         "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": r["cores"],
                          "kind": "oracle",
                          "sample": (f"{r['frames']} whole frame(s)" if r["frames"] else
@@ -644,11 +654,7 @@ def run_ours(args):
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": w["name"], "volume": f"{nx}x{ny}x{nz} {dt}",
-                   "image": f"{W}x{H}", "grad": w["grad"], "step": w["step"],
-                   "skip_empty": w["skip_empty"], "ert": 0.99,
-                   "l2": "flushed between steps (256 MiB write); volume 189 MB > L2",
-                   "parallelism": f"replicas{world}"},
+        "config": bench_config(w, world),
         "frames_per_s": 1000.0 / ms_per_step,
         "phase_ms": {"upload": upload_ms, "tf_camera": tf_ms, "render": render_ms,
                      "records": records_ms, "march": march_avg},
