@@ -413,26 +413,52 @@ __device__ __forceinline__ float4 record_of(const PlaneSums& lo, const PlaneSums
   }
 }
 
-// Stage padded row (y0 - 1 + j, z0 - 1 + k) of brick (x0, y0, z0) from padded x = x0, i.e.
-// voxels x0 - 1 .. x0 + 14, into tile[k][j][0..11]: one aligned 16-element vector (row
-// pitches are multiples of 16 elements and x0 of 8; the vector ends inside the row); rows
-// beyond n are clamped to n (inside the padded border, where E is the edge value).
+// Padded row (y0 - 1 + j, z0 - 1 + k) of brick (x0, y0, z0) from padded x = x0, i.e. voxels
+// x0 - 1 .. x0 + 14, as one aligned 16-element vector of raw words (row pitches are
+// multiples of 16 elements and x0 of 8; the vector ends inside the row); rows beyond n are
+// clamped to n (inside the padded border, where E is the edge value).
 template <int VTYPE>
-__device__ __forceinline__ void stage_row(float (*tile)[11][12], const VolDev& V, int x0, int y0,
-                                          int z0, int j, int k) {
+struct RawRow {
+  static constexpr int kWords = 16 * (int)sizeof(typename VoxelT<VTYPE>::T) / 4;
+  uint32_t w[kWords];
+};
+
+template <int VTYPE>
+__device__ __forceinline__ void load_raw_row(RawRow<VTYPE>& r, const VolDev& V, int x0, int y0,
+                                             int z0, int j, int k) {
   using T = typename VoxelT<VTYPE>::T;
   const int Y = min(y0 - 1 + j, V.n[1]), Z = min(z0 - 1 + k, V.n[2]);
   const T* row = static_cast<const T*>(V.data) + (size_t)V.px * (Y + kPadLo) +
                  (size_t)V.pxy * (Z + kPadLo) + x0;
-  float e[16];
-  if constexpr (VTYPE == VT_U8) {
+  if constexpr (sizeof(T) == 1) {
     const uint2 a0 = __ldg(reinterpret_cast<const uint2*>(row));
     const uint2 a1 = __ldg(reinterpret_cast<const uint2*>(row) + 1);
-    const unsigned wv[4] = {a0.x, a0.y, a1.x, a1.y};
-#pragma unroll
-    for (int i = 0; i < 16; ++i) e[i] = (float)((wv[i >> 2] >> (8 * (i & 3))) & 0xffu);
+    r.w[0] = a0.x; r.w[1] = a0.y; r.w[2] = a1.x; r.w[3] = a1.y;
   } else {
-    load16<VTYPE>(row, e);
+#pragma unroll
+    for (int q = 0; q < RawRow<VTYPE>::kWords / 4; ++q) {
+      const uint4 a = __ldg(reinterpret_cast<const uint4*>(row) + q);
+      r.w[4 * q] = a.x; r.w[4 * q + 1] = a.y; r.w[4 * q + 2] = a.z; r.w[4 * q + 3] = a.w;
+    }
+  }
+}
+
+// Voxels x0 - 1 .. x0 + 10 of a raw row into tile[k][j][0..11].
+template <int VTYPE>
+__device__ __forceinline__ void store_row(float (*tile)[11][12], const RawRow<VTYPE>& r, int j,
+                                          int k) {
+  float e[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    if constexpr (VTYPE == VT_U8) {
+      e[i] = (float)((r.w[i >> 2] >> (8 * (i & 3))) & 0xffu);
+    } else if constexpr (VTYPE == VT_U16 || VTYPE == VT_F16) {
+      const unsigned short h = (unsigned short)((r.w[i >> 1] >> (16 * (i & 1))) & 0xffffu);
+      if constexpr (VTYPE == VT_F16) e[i] = __half2float(__ushort_as_half(h));
+      else e[i] = (float)h;
+    } else {
+      e[i] = __uint_as_float(r.w[i]);
+    }
   }
   float4* dst = reinterpret_cast<float4*>(&tile[k][j][0]);
   dst[0] = make_float4(e[0], e[1], e[2], e[3]);
@@ -469,12 +495,27 @@ __global__ void __launch_bounds__(64) k_records(const VolDev V, const uint8_t* _
   }
   const int nwork = list ? list[0] : nbricks;
   const size_t zstride = (size_t)nx * ny;
+  // rows t and t + 64 of the 121 rows of a brick's neighbourhood; the next brick's rows are
+  // loaded into registers while the current brick is computed
+  const int j0 = t % 11, k0 = t / 11, j1 = (t + 64) % 11, k1 = (t + 64) / 11;
+  const bool has1 = t + 64 < 121;
+  RawRow<VTYPE> ra, rb;
+  auto load_rows = [&](int item) {
+    const int b = list ? list[1 + item] : item;
+    const int x0 = (b % nbx) << kBrickShift, y0 = ((b / nbx) % nby) << kBrickShift,
+              z0 = (b / (nbx * nby)) << kBrickShift;
+    load_raw_row<VTYPE>(ra, V, x0, y0, z0, j0, k0);
+    if (has1) load_raw_row<VTYPE>(rb, V, x0, y0, z0, j1, k1);
+  };
+  if ((int)blockIdx.x < nwork) load_rows(blockIdx.x);
   for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
     const int bid = list ? list[1 + item] : item;
     const int bx = bid % nbx, by = (bid / nbx) % nby, bz = bid / (nbx * nby);
     const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
-    for (int r = t; r < 121; r += 64) stage_row<VTYPE>(tile, V, x0, y0, z0, r % 11, r / 11);
+    store_row<VTYPE>(tile, ra, j0, k0);
+    if (has1) store_row<VTYPE>(tile, rb, j1, k1);
     __syncthreads();
+    if (item + (int)gridDim.x < nwork) load_rows(item + gridDim.x);
     const int x = x0 + u, y = y0 + w;
     if (ncol && x < nx && y < ny) {
       // which of this item's records to write: the core always; a face voxel when the brick
