@@ -285,7 +285,7 @@ def bench_config(w, world):
     return {"workload": w["name"], "volume": f"{nx}x{ny}x{nz} {dtype_name(w['volume'])}",
             "image": f"{cam['width']}x{cam['height']}", "grad": w["grad"], "step": w["step"],
             "skip_empty": w["skip_empty"], "ert": 0.99,
-            "l2": "flushed between steps (256 MiB write); volume 189 MB > L2",
+            "l2": f"flushed between steps (256 MiB write); volume {w['volume'].nbytes / 1e6:.0f} MB",
             "parallelism": f"replicas{world}"}
 
 
