@@ -569,14 +569,12 @@ __global__ void __launch_bounds__(64) k_records(const VolDev V, const uint8_t* _
 template <int VTYPE, int OP>
 static void launch_records_k(const VolDev& V, const uint8_t* need, const int* list, float4* rec,
                              cudaStream_t s) {
-  static int grid = 0;  // persistent grid: SMs x resident blocks (same device for a process)
-  if (grid == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_records<VTYPE, OP>, 64, 0);
-    grid = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
-  }
+  // persistent grid: the current device's SMs x resident blocks
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_records<VTYPE, OP>, 64, 0);
+  const int grid = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
   const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
   k_records<VTYPE, OP><<<min(grid, nbricks), 64, 0, s>>>(V, need, list, rec);
 }
