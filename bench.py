@@ -679,18 +679,20 @@ def run_ours(args):
         line["batch"] = batch_leg(args)
     if not args.no_extras and world == 1:
         # end to end through the C ABI with host buffers: H2D of the volume and TF, D2H of
-        # the image, every step.  Serial: one context, each step waited for.  Pipelined: two
-        # contexts on two streams, so step i's copies overlap step i-1's kernels; the host
-        # reads every step's image (checks a pixel) before its buffer is reused.
+        # the image, every step.  Serial: one context, each step waited for.  Pipelined:
+        # DEPTH contexts on DEPTH streams, so a step's copies overlap the previous steps'
+        # kernels; the host reads every step's image (checks a pixel) before its buffer is
+        # reused.
         from paper_1609_01317_gb300 import Renderer as _R
 
+        DEPTH = 2
         host_vol = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).pin_memory()
         host_tf = torch.from_numpy(w["tf"]).pin_memory()
-        host_out = [torch.empty((H, W, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
-        R2 = _R(local)
-        ctxs = [ctx, R2.ctx]
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-        done = [torch.cuda.Event(), torch.cuda.Event()]
+        host_out = [torch.empty((H, W, 4), dtype=torch.float32).pin_memory() for _ in range(DEPTH)]
+        extra = [_R(local) for _ in range(DEPTH - 1)]
+        ctxs = [ctx] + [r.ctx for r in extra]
+        streams = [torch.cuda.Stream() for _ in range(DEPTH)]
+        done = [torch.cuda.Event() for _ in range(DEPTH)]
 
         def e2e_step(j):
             h = streams[j].cuda_stream
@@ -700,12 +702,13 @@ def run_ours(args):
             vr.vr_render(ctxs[j], params, host_out[j], h)
             done[j].record(streams[j])
 
-        for j in (0, 1, 0, 1):
-            e2e_step(j)
+        for rep in range(2):
+            for j in range(DEPTH):
+                e2e_step(j)
         torch.cuda.synchronize()
         ref_out = out.cpu()
-        ok = torch.equal(host_out[0], ref_out) and torch.equal(host_out[1], ref_out)
-        ke = max(4, min(K, 50))
+        ok = all(torch.equal(o, ref_out) for o in host_out)
+        ke = max(2 * DEPTH, min(K, 60))
         probe = (H // 2, W // 2)
         checks = 0.0
         t0 = time.perf_counter()
@@ -716,22 +719,23 @@ def run_ours(args):
         serial_s = (time.perf_counter() - t0) / ke
         t0 = time.perf_counter()
         for i in range(ke):
-            j = i % 2
-            if i >= 2:
-                done[j].synchronize()  # step i-2 finished: read its image
+            j = i % DEPTH
+            if i >= DEPTH:
+                done[j].synchronize()  # step i - DEPTH finished: read its image
                 checks += float(host_out[j][probe][3])
             e2e_step(j)
-        for j in (0, 1):
+        for j in range(DEPTH):
             done[j].synchronize()
             checks += float(host_out[j][probe][3])
         e2e_s = (time.perf_counter() - t0) / ke
-        ok = ok and torch.equal(host_out[(ke - 1) % 2], ref_out)
-        R2.close()
+        ok = ok and torch.equal(host_out[(ke - 1) % DEPTH], ref_out)
+        for r in extra:
+            r.close()
         line["e2e"] = {"value": samples / e2e_s / 1e9, "unit": "Gsamples/s",
                        "h2d_bytes_per_step": int(vol.nbytes + w["tf"].nbytes),
                        "d2h_bytes_per_step": int(H * W * 16), "ms_per_step": e2e_s * 1e3,
-                       "pipeline": "2 contexts on 2 streams (step i's copies overlap step i-1's "
-                                   "kernels); host reads every step's image",
+                       "pipeline": f"{DEPTH} contexts on {DEPTH} streams (a step's copies overlap "
+                                   "the previous steps' kernels); host reads every step's image",
                        "serial_ms_per_step": serial_s * 1e3,
                        "serial_value": samples / serial_s / 1e9,
                        "steps": ke, "matches_device_result": bool(ok)}
