@@ -278,6 +278,23 @@ def oracle_sample(w, seconds):
             "cores": oracle.num_threads()}
 
 
+def oracle_one_core(w, rows=8):
+    """The FP64 oracle on one host thread over a band of rows in the frame's middle: the
+    per-core rate, in Gsamples/s."""
+    import oracle
+
+    ov = oracle.OracleVolume(w["volume"], w["value_max"])
+    pr = oracle.make_params(step=w["step"], grad=w["grad"])
+    mid = w["camera"]["height"] // 2
+    n0 = oracle.num_threads()
+    t0 = time.perf_counter()
+    _, _, total = oracle.render(ov, w["tf"], w["camera"], pr, rows=(mid - rows // 2, mid + rows // 2),
+                                nthreads=1)
+    dt = time.perf_counter() - t0
+    oracle.render(ov, w["tf"], w["camera"], pr, rows=(mid, mid + 1), nthreads=n0)  # restore
+    return total / dt / 1e9, rows
+
+
 def bench_config(w, world):
     """The workload description shared by both arms' JSON lines."""
     nz, ny, nx = w["volume"].shape
@@ -743,10 +760,13 @@ def run_ours(args):
         cb = oracle_sample(w, args.cpu_seconds)
         what = (f"{cb['frames']} whole frame(s)" if cb["frames"] else
                 f"image rows {cb['rows'][0]}-{cb['rows'][1]}")
+        one, one_rows = oracle_one_core(w)
         line["cpu_baseline"] = {"value": cb["samples"] / cb["seconds"] / 1e9,
                                 "unit": "Gsamples/s", "cores": cb["cores"], "kind": "oracle",
                                 "sample": f"{what} of the workload "
-                                          f"({cb['samples']} samples, {cb['seconds']:.1f} s)"}
+                                          f"({cb['samples']} samples, {cb['seconds']:.1f} s)",
+                                "per_core": {"value": one, "unit": "Gsamples/s",
+                                             "sample": f"{one_rows} middle rows, 1 thread"}}
     else:
         line["e2e"] = None
         line["cpu_baseline"] = None
