@@ -232,3 +232,67 @@ def test_full_size_ct_sampled_pixels(R):
     got = img[pick[:, 0], pick[:, 1]]
     assert_image_parity(got, ref, "ct full size, sampled")
     torch.cuda.synchronize()
+
+
+def test_ct_4k_f16_sampled_pixels(R):
+    """The same phantom stored as FP16 (raw / 4095) at 3840 x 2160 with Sobel3D: sampled
+    pixels against the oracle (2.1x the rays of the benchmark frame, 4x the tiles)."""
+    w = P.workload_ct(width=3840, height=2160)
+    vol = (w["volume"].astype(np.float32) / 4095.0).astype(np.float16)
+    tf, cam = w["tf"], w["camera"]
+    img, _ = gpu_render(R, vol, 1.0, tf, cam, step=0.5, grad="sobel3d", skip_empty=True)
+    hit = np.argwhere(img[..., 3] > 0)
+    assert len(hit) > 200000
+    rng = np.random.default_rng(6)
+    pick = np.concatenate([hit[rng.choice(len(hit), 1200, replace=False)],
+                           rng.integers(0, [cam["height"], cam["width"]], size=(200, 2))])
+    ref, _, _ = oracle.render_pixels(oracle.OracleVolume(vol, 1.0), tf, cam,
+                                     oracle.make_params(step=0.5, grad="sobel3d"),
+                                     pick[:, 1], pick[:, 0])
+    assert_image_parity(img[pick[:, 0], pick[:, 1]], ref, "ct 4k f16, sampled")
+
+
+def test_two_contexts_on_two_streams_overlap_and_agree():
+    """Host-memory uploads and host outputs on two contexts and two streams, interleaved as a
+    pipelined caller would: every frame equals the single-context device render."""
+    import torch
+    from paper_1609_01317_gb300 import Renderer, build, vr
+
+    build.build()
+    vol = P.ellipsoids(61, (96, 80, 72), value_max=4095.0)
+    tf = P.tf_two_plateau(256)
+    cam = P.orbit_camera((96, 80, 72), 160, 120, 0.8, 0.3, 40.0)
+    params = vr.make_params(grad="sobel3d", skip_empty=True)
+    ref_r = Renderer(0)
+    rs = [Renderer(0), Renderer(0)]
+    try:
+        ref_r.upload_volume(vol, 4095.0)
+        ref_r.set_transfer_function(tf)
+        ref_r.set_camera(cam)
+        ref = ref_r.render(params=params).cpu()
+        host_vol = torch.from_numpy(vol.view(np.int16)).pin_memory()
+        host_tf = torch.from_numpy(tf).pin_memory()
+        outs = [torch.full((120, 160, 4), float("nan")).pin_memory() for _ in range(2)]
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        events = [torch.cuda.Event(), torch.cuda.Event()]
+        cs = vr.make_camera(cam)
+        for i in range(8):
+            j = i % 2
+            if i >= 2:
+                events[j].synchronize()
+                assert torch.equal(outs[j], ref), f"frame {i - 2}"
+                outs[j].fill_(float("nan"))
+            h = streams[j].cuda_stream
+            vr.vr_upload_volume(rs[j].ctx, host_vol, "u16", 96, 80, 72, 4095.0, h)
+            vr.vr_set_transfer_function(rs[j].ctx, host_tf, 256, h)
+            vr.vr_set_camera(rs[j].ctx, cs)
+            vr.vr_render(rs[j].ctx, params, outs[j], h)
+            events[j].record(streams[j])
+        for j in range(2):
+            events[j].synchronize()
+            assert torch.equal(outs[j], ref)
+    finally:
+        torch.cuda.synchronize()
+        ref_r.close()
+        for r in rs:
+            r.close()
