@@ -226,8 +226,11 @@ vr_status ensure_records(vr_ctx* ctx, const vr_render_params* p, cudaStream_t s)
   const size_t nvox = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
   void* r = ctx->rec;
   vr_status st = ensure(ctx, &r, &ctx->rec_cap, nvox * sizeof(float4));
-  if (st != VR_OK) return st;
-  ctx->rec = static_cast<float4*>(r);
+  ctx->rec = static_cast<float4*>(r);  // ensure() may have released the old buffer
+  if (st != VR_OK) {
+    ctx->rec_valid = false;
+    return st;
+  }
   st = cuda_status(launch_records(vol_dev(ctx), (int)ctx->dtype, p->grad,
                                   skip ? ctx->brick_vis : nullptr,
                                   skip ? ctx->brick_list : nullptr, ctx->rec, s));
@@ -405,6 +408,10 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const void* src = voxels;
   vr_status st;
+  // until this upload completes the context holds no volume (a failed allocation below may
+  // have released the previous one)
+  ctx->has_volume = false;
+  ctx->rec_valid = false;
   if (!is_device_pointer(voxels)) {
     st = ensure(ctx, &ctx->upload_staging, &ctx->upload_cap, (size_t)nvox * eb);
     if (st != VR_OK) return st;
@@ -428,8 +435,12 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
   const size_t off_list = off_vis + align256(nbricks);
   const size_t off_macro = off_list + align256((nbricks + 1) * sizeof(int));
   st = ensure(ctx, &bt, &ctx->brick_cap, off_macro + nmacro);
-  if (st != VR_OK) return st;
   ctx->brick_minmax = static_cast<float2*>(bt);
+  if (st != VR_OK) {
+    ctx->brick_vis = ctx->macro_vis = nullptr;
+    ctx->brick_list = nullptr;
+    return st;
+  }
   ctx->brick_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) + off_vis);
   ctx->brick_list = reinterpret_cast<int*>(static_cast<char*>(bt) + off_list);
   ctx->macro_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) + off_macro);
@@ -470,11 +481,15 @@ vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, void* 
   DeviceGuard g(ctx->device);
   if (!g.ok) return cuda_status(cudaGetLastError());
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ctx->has_tf = false;  // until this table is in place
   void* buf = ctx->tf;
   const size_t tfb = align256((size_t)n * sizeof(float4));
   vr_status st = ensure(ctx, &buf, &ctx->tf_cap, tfb + (size_t)(n + 1) * sizeof(int));
-  if (st != VR_OK) return st;
   ctx->tf = static_cast<float4*>(buf);
+  if (st != VR_OK) {
+    ctx->tf_prefix = nullptr;
+    return st;
+  }
   ctx->tf_prefix = reinterpret_cast<int*>(static_cast<char*>(buf) + tfb);
   const bool dev = is_device_pointer(rgba);
   st = cuda_status(cudaMemcpyAsync(ctx->tf, rgba, (size_t)n * sizeof(float4),
@@ -619,8 +634,8 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
   if (grad_volume) {
     void* adj = ctx->adj;
     st = ensure(ctx, &adj, &ctx->adj_cap, nvox * sizeof(float4));
-    if (st != VR_OK) return st;
     ctx->adj = static_cast<float4*>(adj);
+    if (st != VR_OK) return st;
     st = cuda_status(cudaMemsetAsync(ctx->adj, 0, nvox * sizeof(float4), s));
     if (st != VR_OK) return st;
   }
@@ -631,8 +646,8 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
     const size_t pbytes = (size_t)ablocks * 4 * ctx->ntf * sizeof(float);
     void* pp = ctx->tf_partial;
     st = ensure(ctx, &pp, &ctx->tf_partial_cap, pbytes);
-    if (st != VR_OK) return st;
     ctx->tf_partial = static_cast<float*>(pp);
+    if (st != VR_OK) return st;
     st = cuda_status(cudaMemsetAsync(ctx->tf_partial, 0, pbytes, s));
     if (st != VR_OK) return st;
   }

@@ -296,3 +296,59 @@ def test_two_contexts_on_two_streams_overlap_and_agree():
         ref_r.close()
         for r in rs:
             r.close()
+
+
+def test_allocator_failure_is_reported_and_the_context_recovers():
+    """An allocator callback that returns NULL makes the call fail with
+    VR_ERR_OUT_OF_MEMORY before any work; once memory is available again the same context
+    renders the frame of a fresh context."""
+    import torch
+    from paper_1609_01317_gb300 import Renderer, build, vr
+
+    build.build()
+    budget = {"left": 1}  # vr_create's own small allocation succeeds, the next one fails
+    live = {}
+
+    def alloc(nbytes, user):
+        if budget["left"] <= 0:
+            return None
+        budget["left"] -= 1
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), 0)
+        live[p] = nbytes
+        return p
+
+    def free(ptr, user):
+        live.pop(ptr, None)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = vr.ALLOC_FN(alloc), vr.FREE_FN(free)
+    ctx = vr.vr_create(0, a, f)
+    vol = P.ellipsoids(62, (40, 36, 30), value_max=4095.0)
+    tf = torch.from_numpy(P.tf_two_plateau(256)).cuda()
+    vd = torch.from_numpy(vol.view(np.int16)).cuda()
+    cam = P.orbit_camera((40, 36, 30), 48, 40, 0.5, 0.3, 40.0)
+    try:
+        with pytest.raises(vr.VrError) as e:
+            vr.vr_upload_volume(ctx, vd, "u16", 40, 36, 30, 4095.0)
+        assert e.value.status == 2
+        budget["left"] = 1_000_000
+        vr.vr_upload_volume(ctx, vd, "u16", 40, 36, 30, 4095.0)
+        vr.vr_set_transfer_function(ctx, tf, 256)
+        vr.vr_set_camera(ctx, vr.make_camera(cam))
+        img = torch.empty((40, 48, 4), device="cuda")
+        p = vr.make_params(grad="sobel3d")
+        vr.vr_render(ctx, p, img)
+        R = Renderer(0)
+        try:
+            R.upload_volume(vol, 4095.0)
+            R.set_transfer_function(P.tf_two_plateau(256))
+            R.set_camera(cam)
+            ref = R.render(params=p)
+            torch.cuda.synchronize()
+            assert torch.equal(img, ref)
+        finally:
+            R.close()
+    finally:
+        torch.cuda.synchronize()
+        vr.vr_destroy(ctx)
+    assert not live  # every buffer the context took went back through the callback
