@@ -305,6 +305,24 @@ vr_status vr_render_batch(vr_ctx *const *vols, const vr_camera *cams, const int 
                           int n, const vr_render_params *params, float *const *outs,
                           void *stream);
 
+/* Measured ceilings of the march (measurement only; renders nothing).  The march is neither
+ * a dense contraction nor HBM-bound, so its roofline is set by the FP32 pipes or by the rate
+ * at which the SMs gather the 8 corner gradient records of a sample (§3.4 trilinear cell,
+ * §3.5 operator gradient) and blend its value and gradient. */
+typedef struct {
+    double fma_tflops;            /* FP32 FMA throughput, TFLOP/s (an FMA counts 2)          */
+    double gather_coherent_gsps;  /* gather + blend, Gsamples/s, the march's access pattern:
+                                     quads of lanes on consecutive samples (step 0.5) of 4 x 2
+                                     neighbouring rays 1.09 voxels apart, table in L2      */
+    double gather_random_gsps;    /* the same at uniformly random cells of a 64 KiB table    */
+} vr_peaks;
+
+/* Time the three microbenchmarks of vr_peaks on `device` (synchronous; private stream and
+ * buffers from cudaMalloc, about 33 MiB, released before returning), best of `repeats`
+ * timed launches after one warm-up.  Errors: INVALID_ARG (out NULL, repeats outside
+ * 1..1000, device < 0), OUT_OF_MEMORY, CUDA (no such device, a launch failed). */
+vr_status vr_measure_peaks(int device, int repeats, vr_peaks *out);
+
 /* Short English text of a status code (static storage). */
 const char *vr_status_string(vr_status status);
 

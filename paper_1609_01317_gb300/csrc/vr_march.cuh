@@ -189,7 +189,8 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
     }
     // Composite the group in sample order with the sequential recurrence of Eq. 6 (the
     // same FP32 operations as a one-sample-at-a-time march, so the grouping -- which
-    // shifts after every skip -- never changes a bit of the result).
+    // shifts after every skip -- never changes a bit of the result).  A zero alpha leaves
+    // C and T bit-identical (its colour is zero and 1 - 0 is exact), so it needs no branch.
     float a4[4], c4[4][3];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -206,13 +207,11 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
         if (CKPT && q == 0 && k + j > 0 && ((k + j) & (kCkptStride - 1)) == 0)
           L.ck_T[(size_t)(((k + j) >> 5) - 1) * (W * H) + ray] = T;
         const float aj = a4[j];
-        if (aj != 0.0f) {
-          const float ta = T * aj;
-          C0 = fmaf(ta, c4[j][0], C0);
-          C1 = fmaf(ta, c4[j][1], C1);
-          C2 = fmaf(ta, c4[j][2], C2);
-          T = T * (1.0f - aj);
-        }
+        const float ta = T * aj;
+        C0 = fmaf(ta, c4[j][0], C0);
+        C1 = fmaf(ta, c4[j][1], C1);
+        C2 = fmaf(ta, c4[j][2], C2);
+        T = T * (1.0f - aj);
         used = j * stride + 1;
         if (1.0f - T >= L.r.ert) stop = true;
       }

@@ -93,6 +93,7 @@ _SIGS = [
     ("vr_render_batch", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(vr_camera), C.POINTER(C.c_int),
                                   C.c_int, C.POINTER(vr_render_params), C.POINTER(C.c_void_p),
                                   C.c_void_p]),
+    ("vr_measure_peaks", C.c_int, [C.c_int, C.c_int, C.c_void_p]),
     ("vr_status_string", C.c_char_p, [C.c_int]),
     ("vr_last_cuda_error", C.c_char_p, []),
     ("vr_version", C.c_int, []),
@@ -287,6 +288,18 @@ def vr_render_batch(vols, cams, vol_of_cam, params, outs, stream=None):
     oarr = (C.c_void_p * n)(*[_ptr(o) for o in outs])
     _check("vr_render_batch", lib().vr_render_batch(varr, cams_arr, idx, n, C.byref(params), oarr,
                                                     stream))
+
+
+class vr_peaks(C.Structure):
+    _fields_ = [("fma_tflops", C.c_double), ("gather_coherent_gsps", C.c_double),
+                ("gather_random_gsps", C.c_double)]
+
+
+def vr_measure_peaks(device=0, repeats=5) -> dict:
+    p = vr_peaks()
+    _check("vr_measure_peaks", lib().vr_measure_peaks(int(device), int(repeats), C.byref(p)))
+    return {"fma_tflops": p.fma_tflops, "gather_coherent_gsps": p.gather_coherent_gsps,
+            "gather_random_gsps": p.gather_random_gsps}
 
 
 def vr_status_string(status) -> str:

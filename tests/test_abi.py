@@ -65,6 +65,10 @@ def test_null_arguments_are_rejected_without_a_device(libvr):
     assert L.vr_render(None, C.byref(p), None, None) == 1
     assert L.vr_render_backward(None, C.byref(p), None, None, None, None, None) == 1
     assert L.vr_read_stats(None, None, None) == 1
+    pk = vr.vr_peaks()
+    assert L.vr_measure_peaks(0, 5, None) == 1
+    assert L.vr_measure_peaks(0, 0, C.byref(pk)) == 1
+    assert L.vr_measure_peaks(-1, 5, C.byref(pk)) == 1
     L.vr_destroy(None)  # no-op
 
 
