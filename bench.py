@@ -702,7 +702,9 @@ def run_ours(args):
         "roofline": roof,
         "roofline_hbm": roof_hbm,
         "roofline_measured": roof_measured,
-        "gpu_launches": 6 * K,
+        # per step: k_pad, k_brick_minmax, k_brick_visibility (upload); k_tf_prefix,
+        # k_brick_visibility (transfer function); k_records, k_march (render)
+        "gpu_launches": 7 * K,
         "wall_s": t_wall,
     }
     line["clocks"] = clk.summary()

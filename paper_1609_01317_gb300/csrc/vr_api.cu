@@ -1,4 +1,5 @@
 // vr_api.cu -- the C ABI of libvr (argument validation, state, memory, launches).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -256,6 +257,54 @@ RecDev rec_dev(const vr_ctx* ctx) {
   return R;
 }
 
+// Pixels whose rays can meet the sampling box [lo, hi]: the bounding rectangle of the
+// box corners projected onto the image (the projection of a convex box in front of the
+// camera is the convex hull of its projected corners), widened by two pixels for the FP32
+// rounding of the ray set-up.  The full image when a corner lies near or behind the eye
+// plane of a perspective camera; empty when the box is empty.
+void screen_rect(const CamDev& c, const float lo[3], const float hi[3], int rect[4]) {
+  const int W = c.width, H = c.height;
+  rect[0] = 0;
+  rect[1] = 0;
+  rect[2] = W;
+  rect[3] = H;
+  for (int a = 0; a < 3; ++a)
+    if (lo[a] > hi[a]) {
+      rect[2] = rect[3] = 0;
+      return;
+    }
+  double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+  for (int k = 0; k < 8; ++k) {
+    const double P[3] = {(k & 1) ? hi[0] : lo[0], (k & 2) ? hi[1] : lo[1], (k & 4) ? hi[2] : lo[2]};
+    double rel[3], u = 0.0, v = 0.0, z = 0.0;
+    for (int a = 0; a < 3; ++a) rel[a] = P[a] - (double)c.eye[a];
+    for (int a = 0; a < 3; ++a) {
+      u += rel[a] * c.right[a];
+      v += rel[a] * c.upv[a];
+      z += rel[a] * c.fwd[a];
+    }
+    if (!c.ortho) {
+      if (!(z > 1e-3)) return;  // near or behind the eye plane: no culling
+      u /= z;
+      v /= z;
+    }
+    const double sx = u / c.ax, sy = v / c.ay;
+    const double x = (sx + 1.0) * 0.5 * W - 0.5, y = (1.0 - sy) * 0.5 * H - 0.5;
+    if (!std::isfinite(x) || !std::isfinite(y)) return;
+    xmin = std::min(xmin, x);
+    xmax = std::max(xmax, x);
+    ymin = std::min(ymin, y);
+    ymax = std::max(ymax, y);
+  }
+  const double x0 = std::floor(xmin) - 2.0, x1 = std::ceil(xmax) + 3.0;
+  const double y0 = std::floor(ymin) - 2.0, y1 = std::ceil(ymax) + 3.0;
+  rect[0] = (int)std::min(std::max(x0, 0.0), (double)W);
+  rect[2] = (int)std::min(std::max(x1, 0.0), (double)W);
+  rect[1] = (int)std::min(std::max(y0, 0.0), (double)H);
+  rect[3] = (int)std::min(std::max(y1, 0.0), (double)H);
+  if (rect[2] <= rect[0] || rect[3] <= rect[1]) rect[0] = rect[1] = rect[2] = rect[3] = 0;
+}
+
 static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* out,
                                int* ck_kend, float* ck_T, int nslots, cudaStream_t s,
                                float* ck_Tend = nullptr) {
@@ -276,6 +325,19 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
   L.ck_T = ck_T;
   L.ck_Tend = ck_Tend;
   L.nslots = nslots;
+  L.rect[0] = L.rect[1] = 0;
+  L.rect[2] = L.cam.width;
+  L.rect[3] = L.cam.height;
+  if (!ck_kend) {
+    // march only the tiles of the box's screen rectangle; the other pixels are zero
+    // (checkpointed renders write every ray's checkpoints, so they march every tile)
+    screen_rect(L.cam, L.r.lo, L.r.hi, L.rect);
+    if (L.rect[0] > 0 || L.rect[1] > 0 || L.rect[2] < L.cam.width || L.rect[3] < L.cam.height) {
+      vr_status st = cuda_status(cudaMemsetAsync(
+          out, 0, (size_t)L.cam.width * L.cam.height * sizeof(float4), s));
+      if (st != VR_OK) return st;
+    }
+  }
   if (p->collect_stats) {
     vr_status st = cuda_status(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
     if (st != VR_OK) return st;

@@ -156,12 +156,18 @@ struct MarchLaunch {
   float4* out;
   unsigned long long* stats;  // NULL: no counting
   unsigned* tile_counter;     // work counter of the persistent launch (zeroed per launch)
+  int rect[4];                // pixels [rect[0], rect[2]) x [rect[1], rect[3]) whose tiles the
+                              // launch marches; every ray outside misses the sampling box
+                              // and its pixel is zeroed beforehand
   int* ck_kend;               // NULL: no checkpoints
   float* ck_T;                // transmittance before every 32nd sample, [slot][ray]
   float* ck_Tend;             // transmittance after the last sample, [ray]
   int nslots;
 };
 cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s);
+// Pixel rectangle [rect[0], rect[2]) x [rect[1], rect[3]) outside which every ray of camera c
+// misses the box [lo, hi] (the full image when that cannot be shown, empty for an empty box).
+void screen_rect(const CamDev& c, const float lo[3], const float hi[3], int rect[4]);
 
 struct AdjointLaunch {
   VolDev V;

@@ -33,16 +33,18 @@ __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
   const int q = lane & 3, qd = lane >> 2;
   const unsigned qmask = 0xFu << (lane & ~3);
   const int W = L.cam.width, H = L.cam.height;
-  const int tiles_x = (W + kTileW - 1) / kTileW;
-  const int tiles = tiles_x * ((H + kTileH - 1) / kTileH);
+  // tiles covering the pixel rectangle L.rect (every ray outside it misses the box)
+  const int tx0 = L.rect[0] / kTileW, ty0 = L.rect[1] / kTileH;
+  const int tiles_x = (L.rect[2] + kTileW - 1) / kTileW - tx0;
+  const int tiles = tiles_x * ((L.rect[3] + kTileH - 1) / kTileH - ty0);
   unsigned hit = 0, plain = 0, visited = 0, shaded = 0;
   for (;;) {
     int tile = 0;
     if (lane == 0) tile = (int)atomicAdd(L.tile_counter, 1u);
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= tiles) break;
-    const int px = (tile % tiles_x) * kTileW + (qd & 3);
-    const int py = (tile / tiles_x) * kTileH + (qd >> 2);
+    const int px = (tx0 + tile % tiles_x) * kTileW + (qd & 3);
+    const int py = (ty0 + tile / tiles_x) * kTileH + (qd >> 2);
     march_ray<CKPT, TFS, ADAPT>(L, px, py, px < W && py < H, q, qmask, hit, plain, visited,
                                 shaded, s_tf);
     __syncwarp();

@@ -34,7 +34,18 @@ struct SurfaceLaunch {
   float4* out;
   float* depth;
   unsigned* counter;
+  int rect[4];  // pixels whose tiles are marched; every other ray misses the sampling box
 };
+
+// No-hit output (0, 0, 0, 0) and depth +inf for every pixel, before a march restricted to
+// the box's screen rectangle.
+__global__ void k_surface_clear(float4* __restrict__ out, float* __restrict__ depth, int n) {
+  const float inf = __int_as_float(0x7f800000);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    out[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (depth) depth[i] = inf;
+  }
+}
 
 // Footprint range [min, max] meets the window, widened by a relative 1e-6 (FP32 lerps of
 // non-integer voxel values may leave the corners' range by an ulp).
@@ -146,15 +157,16 @@ template <int VTYPE, int OP>
 __global__ void __launch_bounds__(128) k_surface(const SurfaceLaunch L) {
   const int lane = threadIdx.x & 31;
   const int W = L.cam.width, H = L.cam.height;
-  const int tiles_x = (W + 7) / 8;
-  const int tiles = tiles_x * ((H + 3) / 4);
+  const int tx0 = L.rect[0] / 8, ty0 = L.rect[1] / 4;
+  const int tiles_x = (L.rect[2] + 7) / 8 - tx0;
+  const int tiles = tiles_x * ((L.rect[3] + 3) / 4 - ty0);
   for (;;) {
     int tile = 0;
     if (lane == 0) tile = (int)atomicAdd(L.counter, 1u);
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= tiles) break;
-    const int px = (tile % tiles_x) * 8 + (lane & 7);
-    const int py = (tile / tiles_x) * 4 + (lane >> 3);
+    const int px = (tx0 + tile % tiles_x) * 8 + (lane & 7);
+    const int py = (ty0 + tile / tiles_x) * 4 + (lane >> 3);
     if (px < W && py < H) surface_ray<VTYPE, OP>(L, px, py);
     __syncwarp();
   }
@@ -277,6 +289,13 @@ extern "C" vr_status vr_render_surface(vr_ctx* ctx, const vr_surface_params* par
   L.counter = counter;
   st = cuda_status(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
   if (st != VR_OK) return st;
+  // march the tiles of the sampling box's screen rectangle; clear the rest first
+  screen_rect(L.cam, L.rlo, L.rhi, L.rect);
+  if (L.rect[0] > 0 || L.rect[1] > 0 || L.rect[2] < L.cam.width || L.rect[3] < L.cam.height) {
+    k_surface_clear<<<surface_grid(), 256, 0, s>>>(L.out, L.depth, (int)npix);
+    st = cuda_status(cudaGetLastError());
+    if (st != VR_OK) return st;
+  }
   switch (ctx->dtype) {
     case VR_U8: launch_surface_op<VT_U8>(L, params->grad, s); break;
     case VR_U16: launch_surface_op<VT_U16>(L, params->grad, s); break;

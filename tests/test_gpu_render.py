@@ -352,3 +352,55 @@ def test_allocator_failure_is_reported_and_the_context_recovers():
         torch.cuda.synchronize()
         vr.vr_destroy(ctx)
     assert not live  # every buffer the context took went back through the callback
+
+
+def test_screen_rectangle_culling_drops_no_ray():
+    """vr_render marches only the tiles of the sampling box's screen rectangle; a
+    checkpointed render marches every tile with the same arithmetic, so the two images must be
+    bit-identical for cameras that put the box anywhere: centred, partly off screen, filling
+    the view, around or inside the eye, wide and narrow fields of view, orthographic, clipped."""
+    import torch
+    from paper_1609_01317_gb300 import Renderer, build, vr
+
+    build.build()
+    shp = (40, 36, 30)
+    vol = P.ellipsoids(71, shp, value_max=4095.0)
+    c = P.volume_centre(shp)
+    d = P.volume_diag(shp)
+    W, H = 96, 64
+    cams = [P.orbit_camera(shp, W, H, a, e, fov, radius_diag=r)
+            for a, e, fov, r in ((0.3, 0.2, 40.0, 2.0), (2.1, -0.7, 40.0, 0.7), (4.0, 1.2, 90.0, 0.55),
+                                 (1.0, 0.1, 120.0, 0.1), (5.5, -0.3, 5.0, 3.0))]
+    cams += [P.camera([c[0] + 1.2 * d, c[1] + 0.3 * d, c[2]], [c[0] + 0.45 * d, c[1] + 0.4 * d, c[2]],
+                      [0, 0, 1], W, H, fov_y_deg=50.0),                      # box off to one side
+             P.camera([c[0], c[1], c[2] + 0.5 * shp[2] + 0.01], [c[0], c[1], c[2] + 100.0],
+                      [0, 1, 0], W, H, fov_y_deg=150.0),                     # eye on a face, looking out
+             P.camera([c[0], c[1] - 2 * d, c[2]], c, [0, 0, 1], W, H, ortho=True, ortho_height=20.0),
+             P.camera([c[0] + 2 * d, c[1], c[2] + 5.0], c, [0, 0, 1], W, H, ortho=True,
+                      ortho_height=300.0),
+             P.camera([c[0] - 0.2 * d, c[1], c[2]], c, [0, 0, 1], W, H, ortho=True,
+                      ortho_height=30.0)]                                     # ortho eye inside
+    clips = [dict(), dict(clip_lo=(5.0, 3.0, 2.0), clip_hi=(17.5, 30.0, 12.0)),
+             dict(clip_lo=(50.0, 0.0, 0.0), clip_hi=(60.0, 35.0, 29.0))]     # last: empty box
+    R = Renderer(0)
+    try:
+        R.upload_volume(vol, 4095.0)
+        R.set_transfer_function(P.tf_two_plateau(256))
+        lit = 0
+        for i, cam in enumerate(cams):
+            R.set_camera(cam)
+            for j, clip in enumerate(clips):
+                p = vr.make_params(grad="sobel3d", **clip)
+                a = torch.full((H, W, 4), float("nan"), device="cuda")
+                vr.vr_render(R.ctx, p, a)
+                nb = vr.vr_checkpoint_bytes(R.ctx, p)
+                ck = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+                off = (-ck.data_ptr()) % 256
+                b = torch.full((H, W, 4), float("nan"), device="cuda")
+                vr.vr_render_forward_train(R.ctx, p, b, ck[off:off + nb], nb)
+                torch.cuda.synchronize()
+                assert torch.equal(a, b), f"camera {i}, clip {j}"
+                lit += int((a[..., 3] > 0).sum().item() > 0)
+        assert lit >= 14  # most views see the volume
+    finally:
+        R.close()

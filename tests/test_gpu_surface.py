@@ -178,3 +178,24 @@ def test_surface_full_size_ct_band():
     assert np.isfinite(o_depth[sl]).sum() > 500
     assert_image_parity(img[sl], o_img[sl], "CT bone band")
     assert np.isfinite(depth).sum() > 10000  # thin bone shells of the phantom
+
+
+def test_surface_screen_rectangle_culling_drops_no_hit():
+    """Only the tiles of the sampling box's screen rectangle are marched; against the oracle
+    (which traces every pixel) for views that put the box off centre, fill the view, surround
+    the eye or clip it."""
+    shp = (30, 26, 22)
+    vol = P.ellipsoids(72, shp, value_max=255.0, dtype=np.uint8)
+    c = P.volume_centre(shp)
+    d = P.volume_diag(shp)
+    W, H = 64, 48
+    cams = [P.orbit_camera(shp, W, H, 2.1, -0.7, 40.0, radius_diag=0.7),
+            P.orbit_camera(shp, W, H, 1.0, 0.1, 120.0, radius_diag=0.1),
+            P.camera([c[0] + 1.2 * d, c[1] + 0.3 * d, c[2]], [c[0] + 0.45 * d, c[1] + 0.4 * d, c[2]],
+                     [0, 0, 1], W, H, fov_y_deg=50.0),
+            P.camera([c[0], c[1] - 2 * d, c[2]], c, [0, 0, 1], W, H, ortho=True, ortho_height=14.0)]
+    lo = float(np.percentile(vol, 60))
+    for i, cam in enumerate(cams):
+        for clip in (dict(), dict(clip_lo=(4.0, 3.0, 2.0), clip_hi=(17.5, 20.0, 12.0))):
+            _check(vol, 255.0, cam, f"cam{i} {clip}", min_hits=1, step=1.0, iso_lo=lo,
+                   iso_hi=3.0e38, refine=4, grad="central", **clip)
