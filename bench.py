@@ -207,11 +207,13 @@ def replica_throughput(samples_per_step, steps, step_ms_total, world):
 
 # ------------------------------------------------------------ ncu traffic record
 KERNEL_SOURCES = {
-    "k_march": ["vr_device.cuh", "vr_march.cuh", "vr_render.cu"],
-    "k_adjoint": ["vr_device.cuh", "vr_adjoint.cu"],
+    "k_march": ["vr_device.cuh", "vr_internal.h", "vr_march.cuh", "vr_render.cu"],
+    "k_adjoint": ["vr_device.cuh", "vr_internal.h", "vr_adjoint.cu"],
+    "k_surface": ["vr_device.cuh", "vr_internal.h", "vr_surface.cu"],
 }
 PROFILE_SUMMARY = {"k_march": "profiles/k_march_ct512x512x361_1080p.md",
-                   "k_adjoint": "profiles/k_adjoint_density128_16views.md"}
+                   "k_adjoint": "profiles/k_adjoint_density128_16views.md",
+                   "k_surface": "profiles/k_surface_ct512x512x361_1080p_bone.md"}
 
 
 def source_hash(kernel):

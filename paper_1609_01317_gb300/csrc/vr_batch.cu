@@ -50,8 +50,14 @@ __global__ void __launch_bounds__(THREADS) k_march_batch(const BatchLaunch B) {
     const int local = tile - __ldg(B.prefix + lo);
     const int W = L.cam.width, H = L.cam.height;
     const int tiles_x = (W + B.tw - 1) / B.tw;
-    const int px = (local % tiles_x) * B.tw + (qd % B.tw);
-    const int py = (local / tiles_x) * B.th + (qd / B.tw);
+    const int x0 = (local % tiles_x) * B.tw, y0 = (local / tiles_x) * B.th;
+    const int px = x0 + (qd % B.tw);
+    const int py = y0 + (qd / B.tw);
+    if (x0 + B.tw <= L.rect[0] || x0 >= L.rect[2] || y0 + B.th <= L.rect[1] || y0 >= L.rect[3]) {
+      // the whole tile lies outside the box's screen rectangle: its rays miss the box
+      if (q == 0 && px < W && py < H) L.out[py * W + px] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      continue;
+    }
     march_ray<false>(L, px, py, px < W && py < H, q, qmask, hit, plain, visited, shaded);
     __syncwarp();
   }
@@ -238,6 +244,7 @@ vr_status vr_batch_create(vr_batch** out, vr_ctx* const* ctxs, int nctx, const v
     L.dtype = (int)c->dtype;
     L.op = params->grad;
     L.out = reinterpret_cast<float4*>(outs[i]);
+    screen_rect(L.cam, L.r.lo, L.r.hi, L.rect);
   }
   void* p = nullptr;
   st = ensure(b->owner, &p, &b->items_cap, sizeof(MarchLaunch) * ncams);
@@ -389,6 +396,7 @@ vr_status vr_render_batch(vr_ctx* const* vols, const vr_camera* cams, const int*
     L.dtype = (int)c->dtype;
     L.op = params->grad;
     L.out = reinterpret_cast<float4*>(outs[i]);
+    screen_rect(L.cam, L.r.lo, L.r.hi, L.rect);
     const long long t = (long long)((L.cam.width + tw - 1) / tw) * ((L.cam.height + th - 1) / th);
     if ((long long)pre[i] + t > 2000000000LL) return VR_ERR_INVALID_ARG;
     pre[i + 1] = pre[i] + (int)t;
