@@ -305,6 +305,24 @@ vr_status vr_render_batch(vr_ctx *const *vols, const vr_camera *cams, const int 
                           int n, const vr_render_params *params, float *const *outs,
                           void *stream);
 
+/* The march's per-sample stages at n caller-given points (a testing and inspection aid;
+ * renders nothing).  pos: n x 3 float32 world points (device memory; a point outside the
+ * volume box uses the nearest cell, as a sample on the box face does).  out: n x 12 float32
+ * (device memory), per point:
+ *   [0]     s = V(p) / value_max, V trilinear in the voxel values (§3.4, Eq. 2),
+ *   [1..4]  the transfer function's RGBA at s (§3.7),
+ *   [5..7]  the operator gradient at p (params->grad: Eq. 3, Eq. 4 or Zucker-Hummel, §3.5),
+ *           scaled so that it estimates ds/dx per voxel,
+ *   [8..10] the Phong colour (§3.8) for params' light and coefficients, viewed along the
+ *           current camera's ray through p (the normal is -g/|g|),
+ *   [11]    the gradient's length.
+ * The same device functions as vr_render's march, on the context's volume, transfer function
+ * and camera; gradient records of every brick are brought up to date on `stream`.
+ * Errors: INVALID_ARG (NULL, n < 0, a host pointer, params), UNSUPPORTED (adaptive),
+ * STATE (no volume, transfer function or camera), OUT_OF_MEMORY, CUDA. */
+vr_status vr_probe_samples(vr_ctx *ctx, const vr_render_params *params, const float *pos, int n,
+                           float *out, void *stream);
+
 /* Measured ceilings of the march (measurement only; renders nothing).  The march is neither
  * a dense contraction nor HBM-bound, so its roofline is set by the FP32 pipes or by the rate
  * at which the SMs gather the 8 corner gradient records of a sample (§3.4 trilinear cell,
@@ -322,6 +340,13 @@ typedef struct {
  * timed launches after one warm-up.  Errors: INVALID_ARG (out NULL, repeats outside
  * 1..1000, device < 0), OUT_OF_MEMORY, CUDA (no such device, a launch failed). */
 vr_status vr_measure_peaks(int device, int repeats, vr_peaks *out);
+
+/* Out-of-range gather and scatter indices met by this context's kernels since vr_create
+ * (a testing aid).  Only a library built with -DVR_DEBUG_BOUNDS checks its indices: each
+ * index outside its buffer is counted and clamped into the buffer, so the access stays in
+ * bounds.  Synchronises `stream`.  Errors: INVALID_ARG (NULL), UNSUPPORTED (a regular build:
+ * *count = 0), CUDA. */
+vr_status vr_read_bounds_violations(vr_ctx *ctx, unsigned long long *count, void *stream);
 
 /* Short English text of a status code (static storage). */
 const char *vr_status_string(vr_status status);

@@ -17,6 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvr.so")
+# the bounds-checked build (-DVR_DEBUG_BOUNDS): every gather / scatter index is tested,
+# counted when out of range and clamped; a testing aid, slower than the regular build
+OUT_DIR_BOUNDS = os.path.join(HERE, "_build_bounds")
+LIB_BOUNDS = os.path.join(HERE, "libvr_bounds.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -43,15 +47,18 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), bounds_checked: bool = False) -> str:
+    out_dir, lib = (OUT_DIR_BOUNDS, LIB_BOUNDS) if bounds_checked else (OUT_DIR, LIB)
+    if bounds_checked:
+        extra = (*extra, "-DVR_DEBUG_BOUNDS")
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sources()
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         [os.path.join(HERE, "..", "include", "vr.h")]
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s, *headers]):
             jobs.append([nvcc(), *_flags(extra), "-c", s, "-o", o])
@@ -64,16 +71,16 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                     sys.stderr.write(" ".join(j) + "\n" + r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed for {j[-3]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), ARCH, "-shared", "-cudart", "static", "-Xcompiler", "-fPIC", *objs,
                "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             raise RuntimeError("linking libvr.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

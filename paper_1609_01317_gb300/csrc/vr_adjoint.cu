@@ -42,6 +42,11 @@ __device__ __forceinline__ AdjCell adj_cell(const VolDev& V, const float p[3]) {
     a.f[i] = p[i] - (float)c;
   }
   a.base = (size_t)ib[0] + (size_t)V.n[0] * ((size_t)ib[1] + (size_t)V.n[1] * ib[2]);
+  // corners reach +1 along every axis longer than one voxel
+  a.base = (size_t)VR_CHECK(V.bounds, a.base, 0,
+                            (long long)V.n[0] * V.n[1] * V.n[2] - 1 -
+                                ((V.n[0] > 1) + (V.n[1] > 1) * (long long)V.n[0] +
+                                 (V.n[2] > 1) * (long long)V.n[0] * V.n[1]));
   return a;
 }
 

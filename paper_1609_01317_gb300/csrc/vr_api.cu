@@ -105,6 +105,7 @@ VolDev vol_dev(const vr_ctx* ctx) {
   V.vis = ctx->brick_vis;
   V.mvis = ctx->macro_vis;
   for (int a = 0; a < 3; ++a) V.nm[a] = ctx->nm[a];
+  V.bounds = ctx->stats + 7;
   return V;
 }
 
@@ -113,6 +114,7 @@ TfDev tf_dev(const vr_ctx* ctx) {
   t.tf = ctx->tf;
   t.n = ctx->ntf;
   t.scale = (float)(ctx->ntf - 1) / ctx->value_max;
+  t.bounds = ctx->stats + 7;
   return t;
 }
 
@@ -254,6 +256,7 @@ RecDev rec_dev(const vr_ctx* ctx) {
   R.sx = ctx->n[0] > 1 ? 1 : 0;
   R.sy = ctx->n[1] > 1 ? ctx->n[0] : 0;
   R.sz = ctx->n[2] > 1 ? ctx->n[0] * ctx->n[1] : 0;
+  R.bounds = ctx->stats + 7;
   return R;
 }
 
@@ -418,6 +421,14 @@ vr_status vr_create(vr_ctx** out, int device, vr_alloc_fn alloc, vr_free_fn free
     return s;
   }
   ctx->stats = static_cast<unsigned long long*>(st);
+  // counters and work queues start at zero (the bounds counter is never reset)
+  const vr_status z = cuda_status(cudaMemset(ctx->stats, 0, 8 * sizeof(unsigned long long)));
+  const vr_status zs = z == VR_OK ? cuda_status(cudaDeviceSynchronize()) : z;
+  if (zs != VR_OK) {
+    ctx_free(ctx, ctx->stats);
+    delete ctx;
+    return zs;
+  }
   *out = ctx;
   return VR_OK;
 }
@@ -780,6 +791,25 @@ vr_status vr_read_stats(vr_ctx* ctx, vr_stats* out, void* stream) {
   out->samples_visited = h[2];
   out->samples_shaded = h[3];
   return VR_OK;
+}
+
+vr_status vr_read_bounds_violations(vr_ctx* ctx, unsigned long long* count, void* stream) {
+  if (!ctx || !count) return VR_ERR_INVALID_ARG;
+  *count = 0;
+#ifndef VR_DEBUG_BOUNDS
+  (void)stream;
+  return VR_ERR_UNSUPPORTED;
+#else
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long h = 0;
+  vr_status st = cuda_status(cudaMemcpyAsync(&h, ctx->stats + 7, sizeof(h), cudaMemcpyDeviceToHost, s));
+  if (st != VR_OK) return st;
+  st = cuda_status(cudaStreamSynchronize(s));
+  if (st == VR_OK) *count = h;
+  return st;
+#endif
 }
 
 const char* vr_status_string(vr_status s) {

@@ -41,6 +41,7 @@ struct VolDev {
   const uint8_t* vis;  // per-brick visibility (1 = some sample may be non-transparent)
   const uint8_t* mvis;  // per-macro-brick visibility (OR over its bricks), or null
   int nm[3];            // macro bricks per axis
+  unsigned long long* bounds = nullptr;  // out-of-range index counter (bounds-checked builds)
 };
 
 // Gradient records over the unpadded grid: rec[x + nx*(y + ny*z)] = (G_x, G_y, G_z, V).
@@ -50,13 +51,41 @@ struct RecDev {
   const float4* rec;
   int n[3];
   int sx, sy, sz;
+  unsigned long long* bounds = nullptr;  // out-of-range index counter (bounds-checked builds)
 };
 
 struct TfDev {
   const float4* tf;
   int n;
   float scale;  // (n - 1) / value_max: raw value -> table coordinate
+  unsigned long long* bounds = nullptr;  // out-of-range index counter (bounds-checked builds)
 };
+
+// ------------------------------------------------------------ bounds checks
+// A build with -DVR_DEBUG_BOUNDS tests the gather and scatter indices of the kernels against
+// their buffers before use: an index outside [lo, hi] is counted in *counter (the context's
+// statistics slot 7, read by vr_read_bounds_violations) and clamped into the range, so the
+// access itself stays in bounds.  Regular builds compile the checks away.
+#ifdef VR_DEBUG_BOUNDS
+__device__ __forceinline__ long long vr_check(unsigned long long* counter, long long i,
+                                              long long lo, long long hi) {
+  if (i >= lo && i <= hi) return i;
+  if (counter) atomicAdd(counter, 1ull);
+  return i < lo ? lo : hi;
+}
+#define VR_CHECK(counter, i, lo, hi) \
+  vr_check((counter), (long long)(i), (long long)(lo), (long long)(hi))
+#else
+#define VR_CHECK(counter, i, lo, hi) (i)
+#endif
+
+// Elements of the padded volume.
+__device__ __forceinline__ long long padded_elems(const VolDev& V) {
+  return (long long)V.pxy * (V.n[2] + kPadLo + kPadHi);
+}
+
+// Largest record index offset of a cell's corners (+x, +y and +z neighbours).
+__device__ __forceinline__ long long corner_span(const RecDev& R) { return R.sx + R.sy + R.sz; }
 
 struct ShadeDev {
   float ka, kd, ks, shininess;
@@ -183,7 +212,8 @@ __device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(
 template <int VTYPE>
 __device__ __forceinline__ float trilinear(const VolDev& V, const Cell& c) {
   const auto* v = static_cast<const typename VoxelT<VTYPE>::T*>(V.data);
-  const int b = c.base, px = V.px, pxy = V.pxy;
+  const int px = V.px, pxy = V.pxy;
+  const int b = (int)VR_CHECK(V.bounds, c.base, 0, padded_elems(V) - 1 - (pxy + px + 1));
   const float c000 = ldv<VTYPE>(v, b), c100 = ldv<VTYPE>(v, b + 1);
   const float c010 = ldv<VTYPE>(v, b + px), c110 = ldv<VTYPE>(v, b + px + 1);
   const float c001 = ldv<VTYPE>(v, b + pxy), c101 = ldv<VTYPE>(v, b + pxy + 1);
@@ -215,6 +245,7 @@ __device__ __forceinline__ TfSample tf_lookup(const TfDev& tf, float s_raw,
   u = fminf(fmaxf(u, 0.0f), top);
   int i = (int)u;
   if (i > tf.n - 2) i = tf.n - 2;
+  i = (int)VR_CHECK(tf.bounds, i, 0, tf.n - 2);
   r.i = i;
   r.w = u - (float)i;
   float4 a, b;
@@ -358,8 +389,10 @@ struct PaddedHood {
 template <int VTYPE, int OP>
 __device__ __forceinline__ void value_and_gradient(const VolDev& V, const Cell& c, float& s,
                                                    float g[3]) {
-  PaddedHood<VTYPE> nb{static_cast<const typename VoxelT<VTYPE>::T*>(V.data),
-                       c.base - 1 - V.px - V.pxy, V.px, V.pxy};
+  // the 4 x 4 x 4 neighbourhood spans offsets 0 .. 3 (1 + px + pxy) from its first voxel
+  const int b0 = (int)VR_CHECK(V.bounds, c.base - 1 - V.px - V.pxy, 0,
+                               padded_elems(V) - 1 - 3 * (1 + V.px + V.pxy));
+  PaddedHood<VTYPE> nb{static_cast<const typename VoxelT<VTYPE>::T*>(V.data), b0, V.px, V.pxy};
   contract_neighbourhood<OP>(nb, c.f, s, g);
 }
 

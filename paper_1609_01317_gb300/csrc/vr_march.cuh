@@ -16,7 +16,9 @@ struct Corners {
 };
 
 __device__ __forceinline__ void corners_load(const RecDev& R, const Cell& c, Corners& k) {
-  const size_t base = (size_t)c.ib[0] + (size_t)R.n[0] * ((size_t)c.ib[1] + (size_t)R.n[1] * c.ib[2]);
+  const size_t base = (size_t)VR_CHECK(
+      R.bounds, (size_t)c.ib[0] + (size_t)R.n[0] * ((size_t)c.ib[1] + (size_t)R.n[1] * c.ib[2]), 0,
+      (long long)R.n[0] * R.n[1] * R.n[2] - 1 - corner_span(R));
   const float4* __restrict__ p = R.rec + base;
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -92,7 +94,7 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
       int b0[3];
       brick_of(L.V, p0, b0);
       const int mi0 = macro_of(L.V, b0);
-      const int m0 = __ldg(L.r.mult + mi0);
+      const int m0 = __ldg(L.r.mult + VR_CHECK(L.V.bounds, mi0, 0, L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1));
       if (m0 > 1 && (k & (m0 - 1)) == 0) {
         const int kl = min(k + 4 * m0 - 1, K - 1);
         float pl[3];
@@ -121,19 +123,21 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
       if (live && stride == 1) {
         int bm[3];
         brick_of(L.V, p, bm);
-        w = __ldg(L.r.mult + macro_of(L.V, bm));
+        w = __ldg(L.r.mult + VR_CHECK(L.V.bounds, macro_of(L.V, bm), 0,
+                                      L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1));
       }
     }
     if (L.r.skip && live) {
       int b[3];
       const int bi = brick_of(L.V, p, b);
-      if (!__ldg(L.V.vis + bi)) {
+      if (!__ldg(L.V.vis + VR_CHECK(L.V.bounds, bi, 0, L.V.nb[0] * L.V.nb[1] * L.V.nb[2] - 1))) {
         // transparent brick: leave it, or its whole macro brick when that is transparent too
         vis = false;
         int shift = kBrickShift;
         if (L.V.mvis) {
           const int m[3] = {b[0] >> kMacroShift, b[1] >> kMacroShift, b[2] >> kMacroShift};
-          if (!__ldg(L.V.mvis + m[0] + L.V.nm[0] * (m[1] + L.V.nm[1] * m[2]))) {
+          if (!__ldg(L.V.mvis + VR_CHECK(L.V.bounds, m[0] + L.V.nm[0] * (m[1] + L.V.nm[1] * m[2]),
+                                         0, L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1))) {
             b[0] = m[0];
             b[1] = m[1];
             b[2] = m[2];

@@ -97,10 +97,11 @@ __device__ __forceinline__ void surface_ray(const SurfaceLaunch& L, int px, int 
     if (L.skip) {
       int b[3];
       const int bi = brick_of(L.V, p, b);
-      if (!__ldg(L.V.vis + bi)) {
+      if (!__ldg(L.V.vis + VR_CHECK(L.V.bounds, bi, 0, L.V.nb[0] * L.V.nb[1] * L.V.nb[2] - 1))) {
         int shift = kBrickShift;
         const int m[3] = {b[0] >> kMacroShift, b[1] >> kMacroShift, b[2] >> kMacroShift};
-        if (!__ldg(L.V.mvis + m[0] + L.V.nm[0] * (m[1] + L.V.nm[1] * m[2]))) {
+        if (!__ldg(L.V.mvis + VR_CHECK(L.V.bounds, m[0] + L.V.nm[0] * (m[1] + L.V.nm[1] * m[2]),
+                                       0, L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1))) {
           b[0] = m[0];
           b[1] = m[1];
           b[2] = m[2];

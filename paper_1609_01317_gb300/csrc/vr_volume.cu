@@ -428,8 +428,9 @@ __device__ __forceinline__ void load_raw_row(RawRow<VTYPE>& r, const VolDev& V, 
                                              int z0, int j, int k) {
   using T = typename VoxelT<VTYPE>::T;
   const int Y = min(y0 - 1 + j, V.n[1]), Z = min(z0 - 1 + k, V.n[2]);
-  const T* row = static_cast<const T*>(V.data) + (size_t)V.px * (Y + kPadLo) +
-                 (size_t)V.pxy * (Z + kPadLo) + x0;
+  const T* row = static_cast<const T*>(V.data) +
+                 VR_CHECK(V.bounds, (size_t)V.px * (Y + kPadLo) + (size_t)V.pxy * (Z + kPadLo) + x0,
+                          0, padded_elems(V) - 16);
   if constexpr (sizeof(T) == 1) {
     const uint2 a0 = __ldg(reinterpret_cast<const uint2*>(row));
     const uint2 a1 = __ldg(reinterpret_cast<const uint2*>(row) + 1);
@@ -529,7 +530,9 @@ __global__ void __launch_bounds__(64) k_records(const VolDev V, const uint8_t* _
         wr_lo = !(ox | oy);
       }
       const int qn = min(kBrick + 1, nz - z0);
-      float4* out = rec + (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z0);
+      const size_t obase = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z0);
+      const long long olast = (long long)nx * ny * nz - 1;
+      float4* out = rec + obase;
       if (wr_lo || (wr_top && qn > kBrick)) {
         if (ncol == 2) {
           const bool two = x + 1 < nx;
@@ -541,9 +544,11 @@ __global__ void __launch_bounds__(64) k_records(const VolDev V, const uint8_t* _
             if (q < qn) {
               plane_sums2<OP>(tile[q + 2], u, w, A[(q + 2) % 3], B[(q + 2) % 3]);
               if (q < kBrick ? wr_lo : wr_top) {
-                out[q * zstride] = record_of<OP>(A[q % 3], A[(q + 1) % 3], A[(q + 2) % 3]);
+                out[VR_CHECK(V.bounds, q * zstride, -(long long)obase, olast - (long long)obase)] =
+                    record_of<OP>(A[q % 3], A[(q + 1) % 3], A[(q + 2) % 3]);
                 if (two)
-                  out[q * zstride + 1] = record_of<OP>(B[q % 3], B[(q + 1) % 3], B[(q + 2) % 3]);
+                  out[VR_CHECK(V.bounds, q * zstride + 1, -(long long)obase, olast - (long long)obase)] =
+                      record_of<OP>(B[q % 3], B[(q + 1) % 3], B[(q + 2) % 3]);
               }
             }
           }
@@ -556,7 +561,8 @@ __global__ void __launch_bounds__(64) k_records(const VolDev V, const uint8_t* _
             if (q < qn) {
               ps[(q + 2) % 3] = plane_sums<OP>(tile[q + 2], u, w);
               if (q < kBrick ? wr_lo : wr_top)
-                out[q * zstride] = record_of<OP>(ps[q % 3], ps[(q + 1) % 3], ps[(q + 2) % 3]);
+                out[VR_CHECK(V.bounds, q * zstride, -(long long)obase, olast - (long long)obase)] =
+                    record_of<OP>(ps[q % 3], ps[(q + 1) % 3], ps[(q + 2) % 3]);
             }
           }
         }

@@ -11,7 +11,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libvr.so")
+# VR_LIBRARY selects another build of the library (the bounds-checked libvr_bounds.so)
+LIB_PATH = os.environ.get("VR_LIBRARY") or os.path.join(HERE, "libvr.so")
 
 VR_OK = 0
 STATUS_NAMES = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_OUT_OF_MEMORY", 3: "VR_ERR_CUDA",
@@ -93,7 +94,10 @@ _SIGS = [
     ("vr_render_batch", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(vr_camera), C.POINTER(C.c_int),
                                   C.c_int, C.POINTER(vr_render_params), C.POINTER(C.c_void_p),
                                   C.c_void_p]),
+    ("vr_probe_samples", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                   C.c_void_p]),
     ("vr_measure_peaks", C.c_int, [C.c_int, C.c_int, C.c_void_p]),
+    ("vr_read_bounds_violations", C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong), C.c_void_p]),
     ("vr_status_string", C.c_char_p, [C.c_int]),
     ("vr_last_cuda_error", C.c_char_p, []),
     ("vr_version", C.c_int, []),
@@ -288,6 +292,17 @@ def vr_render_batch(vols, cams, vol_of_cam, params, outs, stream=None):
     oarr = (C.c_void_p * n)(*[_ptr(o) for o in outs])
     _check("vr_render_batch", lib().vr_render_batch(varr, cams_arr, idx, n, C.byref(params), oarr,
                                                     stream))
+
+
+def vr_probe_samples(ctx, params, pos, n, out, stream=None):
+    _check("vr_probe_samples", lib().vr_probe_samples(ctx, C.byref(params), _ptr(pos), int(n),
+                                                      _ptr(out), stream))
+
+
+def vr_read_bounds_violations(ctx, stream=None) -> int:
+    n = C.c_ulonglong(0)
+    _check("vr_read_bounds_violations", lib().vr_read_bounds_violations(ctx, C.byref(n), stream))
+    return int(n.value)
 
 
 class vr_peaks(C.Structure):

@@ -69,6 +69,9 @@ def test_null_arguments_are_rejected_without_a_device(libvr):
     assert L.vr_measure_peaks(0, 5, None) == 1
     assert L.vr_measure_peaks(0, 0, C.byref(pk)) == 1
     assert L.vr_measure_peaks(-1, 5, C.byref(pk)) == 1
+    cnt = C.c_ulonglong(7)
+    assert L.vr_read_bounds_violations(None, C.byref(cnt), None) == 1
+    assert L.vr_probe_samples(None, C.byref(p), None, 1, None, None) == 1
     L.vr_destroy(None)  # no-op
 
 
