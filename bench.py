@@ -263,21 +263,21 @@ def oracle_sample(w, seconds):
         rows = max(8, int(8 * seconds / max(dt, 1e-3)))
         r0 = max(0, mid - rows // 2)
         t0 = time.perf_counter()
-        _, _, total = oracle.render(ov, w["tf"], cam, pr, rows=(r0, min(H, r0 + rows)))
+        img, _, total = oracle.render(ov, w["tf"], cam, pr, rows=(r0, min(H, r0 + rows)))
         dt = time.perf_counter() - t0
         return {"samples": int(total), "seconds": dt, "rows": [r0, min(H, r0 + rows)],
-                "frames": 0, "cores": oracle.num_threads()}
+                "frames": 0, "cores": oracle.num_threads(), "image": img}
     total, frames = 0, 0
     t0 = time.perf_counter()
     while frames < 4:
-        _, _, n = oracle.render(ov, w["tf"], cam, pr)
+        img, _, n = oracle.render(ov, w["tf"], cam, pr)
         total += n
         frames += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
     return {"samples": int(total), "seconds": dt, "rows": [0, H], "frames": frames,
-            "cores": oracle.num_threads()}
+            "cores": oracle.num_threads(), "image": img}
 
 
 def oracle_one_core(w, rows=8):
@@ -783,6 +783,16 @@ def run_ours(args):
         what = (f"{cb['frames']} whole frame(s)" if cb["frames"] else
                 f"image rows {cb['rows'][0]}-{cb['rows'][1]}")
         one, one_rows = oracle_one_core(w)
+        # error of the GPU frame against the oracle's rendering of the same rows (the
+        # oracle renders rows of the whole image; only those rows are compared)
+        r0, r1 = cb["rows"]
+        gpu = out.cpu().numpy().astype(np.float64)[r0:r1]
+        ref = cb["image"][r0:r1]
+        err = np.abs(gpu - ref).max(axis=-1)
+        line["parity"] = {"reference": "FP64 oracle", "rows": [r0, r1],
+                          "pixels": int(err.size), "max_abs": float(err.max()),
+                          "frac_within_2e-3": float((err <= 2e-3).mean()),
+                          "mean_abs": float(np.abs(gpu - ref).mean())}
         line["cpu_baseline"] = {"value": cb["samples"] / cb["seconds"] / 1e9,
                                 "unit": "Gsamples/s", "cores": cb["cores"], "kind": "oracle",
                                 "sample": f"{what} of the workload "

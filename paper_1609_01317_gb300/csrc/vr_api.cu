@@ -465,6 +465,7 @@ static vr_status mark_host_copy(vr_ctx* ctx, cudaStream_t s) {
 
 vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int nx, int ny,
                            int nz, float value_max, void* stream) {
+  TraceRange trace_("vr_upload_volume");
   if (!ctx || !voxels) return VR_ERR_INVALID_ARG;
   if (nx < 1 || ny < 1 || nz < 1) return VR_ERR_INVALID_ARG;
   if (!(value_max > 0.0f) || !std::isfinite(value_max)) return VR_ERR_INVALID_ARG;
@@ -550,6 +551,7 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
 }
 
 vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, void* stream) {
+  TraceRange trace_("vr_set_transfer_function");
   if (!ctx || !rgba || n < 2 || n > 65536) return VR_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
   if (!g.ok) return cuda_status(cudaGetLastError());
@@ -596,6 +598,7 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cam) {
 }
 
 vr_status vr_render(vr_ctx* ctx, const vr_render_params* params, float* out_rgba, void* stream) {
+  TraceRange trace_("vr_render");
   if (!ctx || !out_rgba) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
@@ -631,6 +634,7 @@ vr_status vr_checkpoint_bytes(vr_ctx* ctx, const vr_render_params* params, size_
 
 vr_status vr_render_forward_train(vr_ctx* ctx, const vr_render_params* params, float* out_rgba,
                                   void* checkpoints, size_t checkpoint_bytes, void* stream) {
+  TraceRange trace_("vr_render_forward_train");
   if (!ctx || !out_rgba || !checkpoints) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
@@ -675,6 +679,7 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
                                    const vr_camera* cams, const void* const* checkpoints,
                                    const float* const* grad_rgba, float* grad_volume,
                                    float* grad_tf, void* stream) {
+  TraceRange trace_("vr_render_backward_views");
   if (!ctx || nviews < 1 || !cams || !checkpoints || !grad_rgba) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;
@@ -769,6 +774,7 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
 vr_status vr_render_backward(vr_ctx* ctx, const vr_render_params* params, const void* checkpoints,
                              const float* grad_rgba, float* grad_volume, float* grad_tf,
                              void* stream) {
+  TraceRange trace_("vr_render_backward");
   if (!ctx || !checkpoints || !grad_rgba) return VR_ERR_INVALID_ARG;
   if (!ctx->has_camera) return VR_ERR_STATE;
   return vr_render_backward_views(ctx, params, 1, &ctx->cam, &checkpoints, &grad_rgba,

@@ -273,6 +273,7 @@ vr_status vr_batch_create(vr_batch** out, vr_ctx* const* ctxs, int nctx, const v
 }
 
 vr_status vr_batch_run(vr_batch* b, void* stream) {
+  TraceRange trace_("vr_batch_run");
   if (!b) return VR_ERR_INVALID_ARG;
   if (!batch_state_current(b)) return VR_ERR_STATE;
   int prev = -1;
@@ -285,6 +286,7 @@ vr_status vr_batch_run(vr_batch* b, void* stream) {
 }
 
 vr_status vr_batch_autotune(vr_batch* b, void* stream, int* chosen) {
+  TraceRange trace_("vr_batch_autotune");
   if (!b) return VR_ERR_INVALID_ARG;
   if (!batch_state_current(b)) return VR_ERR_STATE;
   int prev = -1;
@@ -344,6 +346,7 @@ vr_status vr_batch_autotune(vr_batch* b, void* stream, int* chosen) {
 vr_status vr_render_batch(vr_ctx* const* vols, const vr_camera* cams, const int* vol_of_cam,
                           int n, const vr_render_params* params, float* const* outs,
                           void* stream) {
+  TraceRange trace_("vr_render_batch");
   if (!vols || !cams || !vol_of_cam || n < 1 || !outs) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;

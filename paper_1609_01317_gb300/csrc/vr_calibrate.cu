@@ -152,6 +152,7 @@ struct Timer {
 using namespace vr;
 
 vr_status vr_measure_peaks(int device, int repeats, vr_peaks* out) {
+  TraceRange trace_("vr_measure_peaks");
   if (!out || repeats < 1 || repeats > 1000) return VR_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

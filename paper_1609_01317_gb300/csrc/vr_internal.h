@@ -9,7 +9,19 @@
 #include "../../include/vr.h"
 #include "vr_device.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace vr {
+
+// An NVTX range around one entry point, so that a profiler's timeline shows which library
+// call launched which kernels (header-only NVTX; no cost without an attached tool).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
 
 // One forward pass that wrote adjoint checkpoints (remembered to validate the backward).
 struct CkptRecord {

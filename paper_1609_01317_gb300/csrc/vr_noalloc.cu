@@ -209,6 +209,7 @@ extern "C" vr_status vr_render_noalloc(const void* voxels, vr_dtype dtype, int n
                                        float value_max, const float* tf_rgba, int ntf,
                                        const vr_camera* cam, const vr_render_params* params,
                                        float* out_rgba, void* stream) {
+  TraceRange trace_("vr_render_noalloc");
   if (!voxels || !tf_rgba || !out_rgba) return VR_ERR_INVALID_ARG;
   if (nx < 1 || ny < 1 || nz < 1) return VR_ERR_INVALID_ARG;
   if (!(value_max > 0.0f) || !(value_max < 3.0e38f)) return VR_ERR_INVALID_ARG;

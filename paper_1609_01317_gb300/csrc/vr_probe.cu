@@ -61,6 +61,7 @@ using namespace vr;
 
 vr_status vr_probe_samples(vr_ctx* ctx, const vr_render_params* params, const float* pos, int n,
                            float* out, void* stream) {
+  TraceRange trace_("vr_probe_samples");
   if (!ctx || !pos || !out || n < 0) return VR_ERR_INVALID_ARG;
   vr_status st = check_params(params);
   if (st != VR_OK) return st;

@@ -217,6 +217,7 @@ vr_status check_surface_params(const vr_surface_params* p) {
 
 extern "C" vr_status vr_render_surface(vr_ctx* ctx, const vr_surface_params* params,
                                        float* out_rgba, float* out_depth, void* stream) {
+  TraceRange trace_("vr_render_surface");
   if (!ctx || !out_rgba) return VR_ERR_INVALID_ARG;
   vr_status st = check_surface_params(params);
   if (st != VR_OK) return st;
