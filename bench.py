@@ -768,6 +768,21 @@ def run_ours(args):
             checks += float(host_out[j][probe][3])
         e2e_s = (time.perf_counter() - t0) / ke
         ok = ok and torch.equal(host_out[(ke - 1) % DEPTH], ref_out)
+        # the host link's own rates (plain copies of the same bytes): the bound of any step
+        # that moves the volume in and the image out
+        def copy_ms(dst, src, reps=5):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                dst.copy_(src, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        h2d_ms = copy_ms(vol_dev, host_vol)
+        d2h_ms = copy_ms(host_out[0], out)
         for r in extra:
             r.close()
         line["e2e"] = {"value": samples / e2e_s / 1e9, "unit": "Gsamples/s",
@@ -777,7 +792,11 @@ def run_ours(args):
                                    "the previous steps' kernels); host reads every step's image",
                        "serial_ms_per_step": serial_s * 1e3,
                        "serial_value": samples / serial_s / 1e9,
-                       "steps": ke, "matches_device_result": bool(ok)}
+                       "steps": ke, "matches_device_result": bool(ok),
+                       "link": {"h2d_gbs": vol.nbytes / h2d_ms / 1e6,
+                                "d2h_gbs": H * W * 16 / d2h_ms / 1e6,
+                                "copies_ms": h2d_ms + d2h_ms,
+                                "frac": (h2d_ms + d2h_ms) / (e2e_s * 1e3)}}
         # CPU baseline: the FP64 oracle on a bounded sample of the same workload
         cb = oracle_sample(w, args.cpu_seconds)
         what = (f"{cb['frames']} whole frame(s)" if cb["frames"] else
