@@ -234,6 +234,23 @@ def test_full_size_ct_sampled_pixels(R):
     torch.cuda.synchronize()
 
 
+def test_full_size_ellipsoids_sampled_pixels(R):
+    """256^3 uint16 ellipsoids at 1024 x 1024 with Sobel3D and skipping (the second
+    benchmark workload): sampled pixels against the oracle."""
+    w = P.workload_ellipsoids_256()
+    vol, tf, cam = w["volume"], w["tf"], w["camera"]
+    img, _ = gpu_render(R, vol, 4095.0, tf, cam, step=w["step"], grad=w["grad"], skip_empty=True)
+    hit = np.argwhere(img[..., 3] > 0)
+    assert len(hit) > 20000
+    rng = np.random.default_rng(7)
+    pick = np.concatenate([hit[rng.choice(len(hit), 1500, replace=False)],
+                           rng.integers(0, [cam["height"], cam["width"]], size=(300, 2))])
+    ref, _, _ = oracle.render_pixels(oracle.OracleVolume(vol, 4095.0), tf, cam,
+                                     oracle.make_params(step=w["step"], grad=w["grad"]),
+                                     pick[:, 1], pick[:, 0])
+    assert_image_parity(img[pick[:, 0], pick[:, 1]], ref, "ellipsoids 256, sampled")
+
+
 def test_ct_4k_f16_sampled_pixels(R):
     """The same phantom stored as FP16 (raw / 4095) at 3840 x 2160 with Sobel3D: sampled
     pixels against the oracle (2.1x the rays of the benchmark frame, 4x the tiles)."""
