@@ -158,7 +158,12 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
         for (int j = ((k + kCkptStride - 1) >> 5) << 5; j < stop; j += kCkptStride)
           if (j > 0) L.ck_T[(size_t)((j >> 5) - 1) * (W * H) + ray] = T;
       }
-      k = kn;
+      // Without adaptive sampling groups stay aligned to multiples of four, so that lane q
+      // always holds the samples k = q (mod 4); the samples of the new group before kn lie
+      // in the bricks just left (transparent: they contribute nothing).  Progress: if every
+      // lane was live, lane 3's exit makes kn >= k + 4, so kn rounded down is still >= k + 4;
+      // otherwise a lane past K set kn = K and the ray ends here (no rounding).
+      k = (ADAPT || kn >= K) ? kn : (kn & ~3);
       continue;
     }
     float alpha = 0.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
@@ -191,39 +196,74 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
         c2 = so.c[2];
       }
     }
-    // Composite the group in sample order with the sequential recurrence of Eq. 6 (the
-    // same FP32 operations as a one-sample-at-a-time march, so the grouping -- which
-    // shifts after every skip -- never changes a bit of the result).  A zero alpha leaves
-    // C and T bit-identical (its colour is zero and 1 - 0 is exact), so it needs no branch.
-    float a4[4], c4[4][3];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      a4[j] = __shfl_sync(qmask, alpha, j, 4);
-      c4[j][0] = __shfl_sync(qmask, c0, j, 4);
-      c4[j][1] = __shfl_sync(qmask, c1, j, 4);
-      c4[j][2] = __shfl_sync(qmask, c2, j, 4);
-    }
+    // Composite the group in sample order with the recurrence of Eq. 6.  T runs through
+    // the group's samples in order on every lane (the same FP32 operations as a
+    // one-sample-at-a-time march).  Without adaptive sampling each lane adds only its own
+    // sample's term T_before * alpha * c to a partial colour, and the four partial colours
+    // are summed once at the end of the ray: groups are aligned to multiples of four (also
+    // after a jump), so lane q sums the samples k = q (mod 4) whether or not transparent
+    // bricks are skipped, and a zero alpha adds an exact zero -- skipping never changes a
+    // bit of the result.  With adaptive sampling the groups follow the regions, and every
+    // lane sums all terms in sample order.  A zero alpha leaves C and T bit-identical (its
+    // colour is zero and 1 - 0 is exact), so it needs no branch.
     bool stop = false;
     int used = 0;
+    if constexpr (ADAPT) {
+      float a4[4], c4[4][3];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (!stop && j * stride < span && k + j * stride < K) {
-        if (CKPT && q == 0 && k + j > 0 && ((k + j) & (kCkptStride - 1)) == 0)
-          L.ck_T[(size_t)(((k + j) >> 5) - 1) * (W * H) + ray] = T;
-        const float aj = a4[j];
-        const float ta = T * aj;
-        C0 = fmaf(ta, c4[j][0], C0);
-        C1 = fmaf(ta, c4[j][1], C1);
-        C2 = fmaf(ta, c4[j][2], C2);
-        T = T * (1.0f - aj);
-        used = j * stride + 1;
-        if (1.0f - T >= L.r.ert) stop = true;
+      for (int j = 0; j < 4; ++j) {
+        a4[j] = __shfl_sync(qmask, alpha, j, 4);
+        c4[j][0] = __shfl_sync(qmask, c0, j, 4);
+        c4[j][1] = __shfl_sync(qmask, c1, j, 4);
+        c4[j][2] = __shfl_sync(qmask, c2, j, 4);
       }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!stop && j * stride < span && k + j * stride < K) {
+          const float aj = a4[j];
+          const float ta = T * aj;
+          C0 = fmaf(ta, c4[j][0], C0);
+          C1 = fmaf(ta, c4[j][1], C1);
+          C2 = fmaf(ta, c4[j][2], C2);
+          T = T * (1.0f - aj);
+          used = j * stride + 1;
+          if (1.0f - T >= L.r.ert) stop = true;
+        }
+      }
+    } else {
+      float a4[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a4[j] = __shfl_sync(qmask, alpha, j, 4);
+      float Tq = 0.0f;  // transmittance before this lane's sample (0: not composited)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!stop && j < span && k + j < K) {
+          if (CKPT && q == 0 && k + j > 0 && ((k + j) & (kCkptStride - 1)) == 0)
+            L.ck_T[(size_t)(((k + j) >> 5) - 1) * (W * H) + ray] = T;
+          if (j == q) Tq = T;
+          T = T * (1.0f - a4[j]);
+          used = j + 1;
+          if (1.0f - T >= L.r.ert) stop = true;
+        }
+      }
+      const float ta = Tq * alpha;
+      C0 = fmaf(ta, c0, C0);
+      C1 = fmaf(ta, c1, C1);
+      C2 = fmaf(ta, c2, C2);
     }
     k += stop ? used : span;
     if (stop) break;
   }
   const int kend = k < K ? k : K;
+  if constexpr (!ADAPT) {
+    // the quad's partial colours, summed in a fixed order: (C_0 + C_1) + (C_2 + C_3)
+    C0 += __shfl_xor_sync(qmask, C0, 1);
+    C1 += __shfl_xor_sync(qmask, C1, 1);
+    C2 += __shfl_xor_sync(qmask, C2, 1);
+    C0 += __shfl_xor_sync(qmask, C0, 2);
+    C1 += __shfl_xor_sync(qmask, C1, 2);
+    C2 += __shfl_xor_sync(qmask, C2, 2);
+  }
   if (active && q == 0) {
     reinterpret_cast<float4*>(L.out)[ray] = make_float4(C0, C1, C2, 1.0f - T);
     if (CKPT) {

@@ -76,6 +76,10 @@ def test_adaptive_parity(dtype, vmax, grad):
             img, st = _render_gpu(vol, vmax, tf, cam, p)
             assert_image_parity(img, ref, f"{dtype.__name__} {grad} cam{i} skip{skip}")
             assert abs(st["samples_plain"] - total) <= max(2, 1e-4 * total)
+            # coarse regions of this volume are visible: fewer samples are evaluated
+            _, st_reg = _render_gpu(vol, vmax, tf, cam,
+                                    vr.make_params(grad=grad, skip_empty=skip, collect_stats=True))
+            assert st["samples_visited"] < st_reg["samples_visited"]
     # the multipliers really vary over this volume
     regular, _, _ = oracle.render(oracle.OracleVolume(vol, vmax), tf, cam,
                                   oracle.make_params(grad=grad))
@@ -104,8 +108,9 @@ def test_adaptive_skipping_bit_identical_and_fewer_samples():
         torch.cuda.synchronize()
         assert torch.equal(outs[0], outs[1])
         assert stats[0]["samples_plain"] == stats[1]["samples_plain"]
-        # fewer samples taken (here in transparent air regions, so the image may not change)
-        assert stats[1]["samples_visited"] < st_plain["samples_visited"]
+        # the coarse regions of this phantom are transparent air, which skipping leaves
+        # anyway: adaptive sampling evaluates no more samples than the regular march
+        assert stats[1]["samples_visited"] <= st_plain["samples_visited"]
     finally:
         r.close()
 
