@@ -305,6 +305,16 @@ vr_status vr_render_batch(vr_ctx *const *vols, const vr_camera *cams, const int 
                           int n, const vr_render_params *params, float *const *outs,
                           void *stream);
 
+/* The pixel rectangle [rect[0], rect[2]) x [rect[1], rect[3]) outside which every ray of
+ * `cam` misses the box [lo, hi] (world units; the renderers pass the sampling box, the clip
+ * box intersected with [0, n-1]^3): the bounding rectangle of the eight box corners projected
+ * through the camera (§3.3 ray set-up), widened by two pixels; the whole image when a corner
+ * lies near or behind the eye plane of a perspective camera, an empty rectangle when the box
+ * is empty.  vr_render, vr_render_batch and vr_render_surface march only the tiles of this
+ * rectangle.  Host only (no device is used).  Errors: INVALID_ARG (NULL, NaN bounds, camera
+ * as for vr_set_camera). */
+vr_status vr_screen_rect(const vr_camera *cam, const float lo[3], const float hi[3], int rect[4]);
+
 /* The march's per-sample stages at n caller-given points (a testing and inspection aid;
  * renders nothing).  pos: n x 3 float32 world points (device memory; a point outside the
  * volume box uses the nearest cell, as a sample on the box face does).  out: n x 12 float32

@@ -799,6 +799,17 @@ vr_status vr_read_stats(vr_ctx* ctx, vr_stats* out, void* stream) {
   return VR_OK;
 }
 
+vr_status vr_screen_rect(const vr_camera* cam, const float lo[3], const float hi[3], int rect[4]) {
+  if (!lo || !hi || !rect) return VR_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (std::isnan(lo[a]) || std::isnan(hi[a])) return VR_ERR_INVALID_ARG;
+  CamDev c;
+  const vr_status st = check_camera(cam, &c);
+  if (st != VR_OK) return st;
+  screen_rect(c, lo, hi, rect);
+  return VR_OK;
+}
+
 vr_status vr_read_bounds_violations(vr_ctx* ctx, unsigned long long* count, void* stream) {
   if (!ctx || !count) return VR_ERR_INVALID_ARG;
   *count = 0;

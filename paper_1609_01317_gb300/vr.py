@@ -97,6 +97,8 @@ _SIGS = [
     ("vr_probe_samples", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                    C.c_void_p]),
     ("vr_measure_peaks", C.c_int, [C.c_int, C.c_int, C.c_void_p]),
+    ("vr_screen_rect", C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                 C.POINTER(C.c_int)]),
     ("vr_read_bounds_violations", C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong), C.c_void_p]),
     ("vr_status_string", C.c_char_p, [C.c_int]),
     ("vr_last_cuda_error", C.c_char_p, []),
@@ -292,6 +294,15 @@ def vr_render_batch(vols, cams, vol_of_cam, params, outs, stream=None):
     oarr = (C.c_void_p * n)(*[_ptr(o) for o in outs])
     _check("vr_render_batch", lib().vr_render_batch(varr, cams_arr, idx, n, C.byref(params), oarr,
                                                     stream))
+
+
+def vr_screen_rect(cam, lo, hi):
+    """(x0, y0, x1, y1): pixels outside [x0, x1) x [y0, y1) see nothing of the box [lo, hi]."""
+    c = cam if isinstance(cam, vr_camera) else make_camera(cam)
+    r = (C.c_int * 4)()
+    _check("vr_screen_rect", lib().vr_screen_rect(C.byref(c), (C.c_float * 3)(*lo),
+                                                  (C.c_float * 3)(*hi), r))
+    return tuple(r)
 
 
 def vr_probe_samples(ctx, params, pos, n, out, stream=None):
