@@ -688,6 +688,7 @@ def run_ours(args):
     line = {
         "metric": "Gsamples/s", "value": value, "unit": "Gsamples/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "ms_per_step_median": statistics.median(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": bench_config(w, world),
