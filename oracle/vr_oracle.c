@@ -51,7 +51,7 @@
  *      or normalize(eye - p) (perspective); diff = max(0, N.L); spec = (N.L > 0) ?
  *      max(0, R.V)^shininess : 0 with R = 2 (N.L) N - L; c = rgb (ka + kd diff) + ks spec.
  *   R9 front to back: C += T a c, T *= (1 - a); stop after the sample where 1 - T >= ert
- *      ("until an alpha of 0 is hit" read as transmittance -> 0).  Output (C, 1 - T),
+ *      (§3.9's end of the recursion at zero alpha read as transmittance -> 0).  Output (C, 1 - T),
  *      premultiplied over black.  Shading is skipped where a == 0 (it adds nothing).
  *
  *   R16 adaptive sampling (§5.2: coarser sampling in detail-poor regions): the regions are
