@@ -137,7 +137,8 @@ void vr_destroy(vr_ctx *ctx);
  * 12-bit u16, 1 for f16/f32).  The library stores a copy with a clamp-to-edge border and
  * per-brick (8^3) min/max tables; if a transfer function is set, brick visibility is
  * recomputed.  Errors: INVALID_ARG (NULL, a size < 1, nx*ny*nz > 2^31, value_max <= 0),
- * UNSUPPORTED (dtype), OUT_OF_MEMORY, CUDA. */
+ * UNSUPPORTED (dtype), OUT_OF_MEMORY, CUDA; after OUT_OF_MEMORY or CUDA the context holds no
+ * volume until an upload succeeds. */
 vr_status vr_upload_volume(vr_ctx *ctx, const void *voxels, vr_dtype dtype, int nx, int ny,
                            int nz, float value_max, void *stream);
 
@@ -145,7 +146,8 @@ vr_status vr_upload_volume(vr_ctx *ctx, const void *voxels, vr_dtype dtype, int 
  * device memory, entry i covering s = i / (n - 1), read with linear interpolation between
  * entries.  Values are used as given (no clamping of alpha).  Recomputes the per-brick
  * visibility flags when a volume is present.  Errors: INVALID_ARG (NULL, n < 2,
- * n > 65536), OUT_OF_MEMORY, CUDA. */
+ * n > 65536), OUT_OF_MEMORY, CUDA; after OUT_OF_MEMORY or CUDA the context holds no transfer
+ * function until a set succeeds. */
 vr_status vr_set_transfer_function(vr_ctx *ctx, const float *rgba, int n, void *stream);
 
 /* Set the camera used by the following renders (host struct, copied).
