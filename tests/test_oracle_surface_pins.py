@@ -193,3 +193,49 @@ def test_first_hit_index_matches_independent_trilinear_scan():
             assert abs(depth[py, px] - (tn + k * step)) <= 1e-4 * max(1.0, tn + k * step)
             checked += 1
     assert checked > 100
+
+
+@pytest.mark.parametrize("refine", [0, 3, 6])
+def test_curved_surface_within_bisection_bound_of_the_exact_root(refine):
+    # a ball-like field v = 2000 + 100 (R - r) (integers, clamped): the window [2000, inf)
+    # is a curved surface.  For rays that cross it well inside (no grazing), the exact first
+    # root of the trilinear interpolant along the ray -- found independently with scipy's
+    # trilinear interpolation on a fine grid and a bracketing root finder -- lies in the
+    # coarse bracket, so the hit must be within step / 2^(R+1) of it
+    from scipy import optimize
+
+    n, R = 48, 15.0
+    c = (n - 1) / 2.0
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=np.float64),) * 3, indexing="ij")
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    vol = np.clip(np.rint(2000.0 + 100.0 * (R - r)), 0, 4095).astype(np.uint16)
+    ov = oracle.OracleVolume(vol, 4095.0)
+    vf = vol.astype(np.float64)
+    cam = P.camera([c - 70.0, c + 9.0, c - 6.0], [c, c, c], [0, 0, 1], 32, 24, fov_y_deg=24.0)
+    step = 1.0
+    iso = 2000.0
+    sp = oracle.make_surface_params(step=step, iso_lo=iso, iso_hi=1e9, refine=refine)
+    _, depth, _ = oracle.render_surface(ov, cam, sp)
+
+    def f(t, o, d):
+        p = o + t * d
+        return ndimage.map_coordinates(vf, p[::-1].reshape(3, 1), order=1, mode="nearest")[0] - iso
+
+    errs = []
+    for py in range(24):
+        for px in range(32):
+            o, d, tn, K, hit = ray_of(cam, step, px, py, (n, n, n))
+            if not hit or K == 0:
+                continue
+            ctr = np.array([c, c, c])
+            miss = np.linalg.norm(np.cross(ctr - o, d))  # distance of the ray from the centre
+            if miss > 0.7 * R:
+                continue  # grazing rays may cross in and out within one step
+            ts = tn + (np.arange(K) + 0.5) * step
+            vals = np.array([f(t, o, d) for t in ts])
+            k = int(np.nonzero(vals >= 0)[0][0])
+            assert k > 0  # the entry point lies outside the ball
+            t_star = optimize.brentq(f, ts[k - 1], ts[k], args=(o, d), xtol=1e-10)
+            errs.append(abs(depth[py, px] - t_star))
+    assert len(errs) > 150
+    assert max(errs) <= step / 2 ** (refine + 1) + 1e-3
