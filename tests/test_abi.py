@@ -92,3 +92,17 @@ def test_renderer_refuses_to_run_without_cuda():
 
     with pytest.raises(RuntimeError):
         Renderer(0)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: with the library absent every call raises."""
+    import subprocess
+    import sys
+
+    env = dict(os.environ, VR_LIBRARY=str(tmp_path / "absent_libvr.so"))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1609_01317_gb300 import vr\n"
+            "try:\n    vr.vr_version()\nexcept RuntimeError as e:\n    print('raised', e)\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0 and "raised" in r.stdout and "missing" in r.stdout
