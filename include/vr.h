@@ -159,7 +159,10 @@ vr_status vr_set_camera(vr_ctx *ctx, const vr_camera *cam);
  * host or device memory, detected; host output is copied back on `stream` and is valid
  * once the stream is synchronised).  Errors: INVALID_ARG (NULL, step <= 0, ert_threshold
  * <= 0, shininess < 0, grad out of range, non-finite parameters), STATE (no volume, TF or
- * camera), OUT_OF_MEMORY, CUDA.  An empty clip box gives a black transparent image. */
+ * camera), OUT_OF_MEMORY, CUDA.  An empty clip box gives a black transparent image.
+ * Every pixel is written: rays are marched only over the tiles of the sampling box's screen
+ * rectangle (vr_screen_rect), and the pixels outside it, whose rays miss the box, are
+ * cleared to (0, 0, 0, 0) first. */
 vr_status vr_render(vr_ctx *ctx, const vr_render_params *params, float *out_rgba, void *stream);
 
 /* Bytes of the checkpoint buffer vr_render_forward_train needs for the current camera,
