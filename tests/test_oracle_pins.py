@@ -411,9 +411,11 @@ def _np_ray(cam, shp, px, py, step, clip_lo, clip_hi):
     return o, d, tn
 
 
-def _np_render(arr, vmax, tf, cam, step, op, ert, clip_lo=(-1e30,) * 3, clip_hi=(1e30,) * 3):
+def _np_render(arr, vmax, tf, cam, step, op, ert, clip_lo=(-1e30,) * 3, clip_hi=(1e30,) * 3,
+               light=None):
     """Naive dense march: no box clipping, alpha forced to 0 outside the box, scipy
-    trilinear (clamp-to-edge), numpy interp for the transfer function, taps summed."""
+    trilinear (clamp-to-edge), numpy interp for the transfer function, taps summed.
+    light: None = headlight (the light at the eye), else a fixed point-light position."""
     from scipy.ndimage import map_coordinates
 
     nz, ny, nx = arr.shape
@@ -471,7 +473,7 @@ def _np_render(arr, vmax, tf, cam, step, op, ert, clip_lo=(-1e30,) * 3, clip_hi=
                 g = grad(p)
                 gn = np.linalg.norm(g)
                 Nn = -g / gn if gn > 1e-6 else np.zeros(3)
-                L = eye - p
+                L = (eye if light is None else np.asarray(light, np.float64)) - p
                 L /= np.linalg.norm(L)
                 V = -d if cam["ortho"] else (eye - p) / np.linalg.norm(eye - p)
                 nl = Nn @ L
@@ -504,6 +506,33 @@ def test_whole_image_brute_force_8cube(op, ortho):
     ref = _np_render(arr, 255.0, tf.astype(np.float64), cam, 0.5, op, 0.95)
     assert (counts > 0).sum() > 30
     np.testing.assert_allclose(img, ref, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("ortho", [True, False])
+@pytest.mark.parametrize("light", [(-1000.0, -1000.0, -1000.0), (1000.0, 1000.0, 1000.0),
+                                   (11.0, -2.5, 3.0)])
+def test_whole_image_fixed_point_light(ortho, light):
+    """§3.8: a point light at a fixed position (the paper's (-1000, -1000, -1000) and
+    (1000, 1000, 1000), and one beside the volume) instead of the headlight: L points from
+    the sample to the light, V from the sample to the eye.  A light vector taken from the
+    eye, or pointing from the light to the sample, fails this."""
+    arr = P.random_volume(65, (8, 8, 8), np.uint8, 255.0)
+    tf = P.tf_random(66, 16, alpha_max=0.35, zero_below=3)
+    shp = (8, 8, 8)
+    if ortho:
+        cam = P.orbit_camera(shp, 12, 10, 0.9, 0.3, ortho=True, ortho_height=12.0)
+    else:
+        cam = P.orbit_camera(shp, 12, 10, -2.3, 0.5, 40.0, radius_diag=1.2)
+    pr = oracle.make_params(step=0.5, grad="sobel3d", ert_threshold=0.97, light=light,
+                            headlight=False)
+    img, counts, _ = oracle.render(_vol(arr, 255.0), tf, cam, pr)
+    ref = _np_render(arr, 255.0, tf.astype(np.float64), cam, 0.5, "sobel3d", 0.97, light=light)
+    assert (counts > 0).sum() > 30
+    np.testing.assert_allclose(img, ref, rtol=0, atol=1e-10)
+    # the light really matters here: the headlight gives a different image
+    head, _, _ = oracle.render(_vol(arr, 255.0), tf, cam,
+                               oracle.make_params(step=0.5, grad="sobel3d", ert_threshold=0.97))
+    assert np.abs(head - img).max() > 1e-3
 
 
 def test_clip_box_cuts_the_volume():

@@ -125,8 +125,10 @@ def _phong_closed_form(N, L, V, rgb, ka=0.1, kd=0.7, ks=0.2, n=20.0):
     return rgb * (ka + kd * max(nl, 0.0)) + ks * spec
 
 
+@pytest.mark.parametrize("light", [None, (-1000.0, -1000.0, -1000.0), (1000.0, 1000.0, 1000.0),
+                                   (-10.0, 60.0, -5.0)])
 @pytest.mark.parametrize("case", ["rising", "falling"])
-def test_plane_shading_closed_form_two_sided(case):
+def test_plane_shading_closed_form_two_sided(case, light):
     # rising: v = 100 + 20x, window [700, inf): plane x = 30 entered from below the window
     # falling: v = 3000 - 20x on a 128-wide volume, window [700, 1000]: plane x = 100 entered
     # from above it -- the outward normal faces away and must be turned to the viewer
@@ -137,10 +139,16 @@ def test_plane_shading_closed_form_two_sided(case):
     ov = oracle.OracleVolume(vol, 4095.0)
     cam = P.camera([-40.0, 19.0, 23.0], [127.0, 19.5, 23.5], [0, 0, 1], 24, 16, fov_y_deg=25.0)
     rgb = np.array([0.9, 0.6, 0.3])
+    # light None: the headlight; else a point light at a fixed position (§3.8: the paper's
+    # (-1000, -1000, -1000) and (1000, 1000, 1000), and one near the plane), where L points
+    # from the hit to the light and V from the hit to the eye
+    kw = {} if light is None else {"light": light, "headlight": False}
     sp = oracle.make_surface_params(step=1.0, iso_lo=lo, iso_hi=hi, refine=8, color=tuple(rgb),
-                                    grad="central")
+                                    grad="central", **kw)
     img, depth, _ = oracle.render_surface(ov, cam, sp)
     eye = np.array(cam["eye"], np.float64)
+    lpos = eye if light is None else np.array(light, np.float64)
+    lit = 0
     checked = 0
     for py in range(cam["height"]):
         for px in range(cam["width"]):
@@ -150,12 +158,16 @@ def test_plane_shading_closed_form_two_sided(case):
             assert abs(depth[py, px] - (xp - o[0]) / d[0]) <= 1.0 / 2 ** 9 + 1e-3
             p = o + float(depth[py, px]) * d
             N = np.array([-1.0, 0.0, 0.0])  # faces the camera, which looks along +x
-            L = (eye - p) / np.linalg.norm(eye - p)
-            want = _phong_closed_form(N, L, L, rgb)
+            L = (lpos - p) / np.linalg.norm(lpos - p)
+            V = (eye - p) / np.linalg.norm(eye - p)
+            want = _phong_closed_form(N, L, V, rgb)
             np.testing.assert_allclose(img[py, px, :3], want, rtol=0, atol=1e-12)
             assert img[py, px, 3] == 1.0
+            lit += float(N @ L) > 0
             checked += 1
     assert checked > 100  # rays that leave through the y / z faces first see no plane
+    if light is None or light[0] < 0:
+        assert lit == checked  # the lit side: diffuse (and specular) terms are exercised
 
 
 def test_first_hit_index_matches_independent_trilinear_scan():
