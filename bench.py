@@ -40,7 +40,6 @@ sys.path.insert(0, ROOT)
 FLOPS_VISIT = 34
 FLOPS_SHADE = {"central": 96, "sobel3d": 392, "zucker_hummel": 392}
 FP32_LANES_PER_SM = 128
-SMS = 152
 
 
 def parse():
@@ -650,7 +649,8 @@ def run_ours(args):
     # defined by FLOPS_VISIT / FLOPS_SHADE
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     flops = stats["samples_visited"] * FLOPS_VISIT + stats["samples_shaded"] * FLOPS_SHADE[w["grad"]]
     achieved = flops / (march_avg / 1e3) / 1e12
     bpv = {"u8": 1, "u16": 2, "f16": 2, "f32": 4}[dt]
@@ -659,7 +659,7 @@ def run_ours(args):
     records_ms = max(render_ms - march_avg, 0.0)
     roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": achieved / alu_peak, "traffic": profiled_traffic("k_march"),
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
             "kernel": "k_march", "launch_ms": march_avg,
             "flops_per_launch": flops,
             "frac_incl_records": flops / ((march_avg + records_ms) / 1e3) / 1e12 / alu_peak}

@@ -24,6 +24,11 @@
  *     the allocator given to vr_create and are released by vr_destroy.
  *   - Volumes are dense x-fastest arrays: voxel (x, y, z) is element x + nx*(y + ny*z)
  *     and sits at world point (x, y, z) (unit spacing, §2.1 Eq. 1).
+ *   - Alignment: a voxel array must be aligned to its element size; device images, image
+ *     gradients and a transfer function read in place (vr_render_noalloc) are accessed as
+ *     16-byte RGBA vectors and must be 16-byte aligned; other device float arrays (volume
+ *     and table gradients, depths, probe points) 4-byte aligned.  A misaligned pointer is
+ *     rejected with VR_ERR_INVALID_ARG before any work is queued.
  *   - Images are H x W x 4 float32 RGBA, row-major, row 0 at the top; RGB is
  *     premultiplied over black and A = 1 - transmittance.
  *   - A context may be used from one host thread at a time, and its calls must be ordered
@@ -246,9 +251,12 @@ vr_status vr_render_surface(vr_ctx *ctx, const vr_surface_params *params, float 
  * GPU (different streams, or other host threads) race and must be serialised by the
  * caller.  The first call on a device looks up the array's device address (host code
  * cannot use the array's name as a device pointer); make that first call before any
- * stream capture.  collect_stats must be 0 (VR_ERR_UNSUPPORTED otherwise).
- * Errors: INVALID_ARG (NULL or host pointers, sizes out of range or beyond the scratch
- * limits, invalid camera or parameters), UNSUPPORTED, CUDA. */
+ * stream capture.  collect_stats and adaptive (§5.2 adaptive sampling) must be 0: this
+ * entry point counts no samples and marches only the regular grid (VR_ERR_UNSUPPORTED
+ * otherwise).  `voxels` must be aligned to its element size, `tf_rgba` and `out_rgba` to
+ * 16 bytes (they are read and written as float4).
+ * Errors: INVALID_ARG (NULL, host or misaligned pointers, sizes out of range or beyond the
+ * scratch limits, invalid camera or parameters), UNSUPPORTED, CUDA. */
 vr_status vr_render_noalloc(const void *voxels, vr_dtype dtype, int nx, int ny, int nz,
                             float value_max, const float *tf_rgba, int ntf,
                             const vr_camera *cam, const vr_render_params *params,

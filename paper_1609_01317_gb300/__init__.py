@@ -98,7 +98,6 @@ class Renderer:
         if hasattr(volume, "dtype") and isinstance(volume, torch.Tensor):
             t = volume.contiguous()
             name = dtype or _dtype_name(t)
-            ptr = t.data_ptr()
             self._vol_ref = t
         else:
             import numpy as np
@@ -106,10 +105,10 @@ class Renderer:
             a = np.ascontiguousarray(volume)
             name = dtype or {np.dtype(np.uint8): "u8", np.dtype(np.uint16): "u16",
                              np.dtype(np.float16): "f16", np.dtype(np.float32): "f32"}[a.dtype]
-            ptr = a.ctypes.data
             self._vol_ref = a
         nz, ny, nx = volume.shape
-        vr.vr_upload_volume(self.ctx, ptr, name, nx, ny, nz, value_max, _stream_handle())
+        vr.vr_upload_volume(self.ctx, self._vol_ref, name, nx, ny, nz, value_max,
+                            _stream_handle())
         self.shape_xyz = (nx, ny, nz)
         self.value_max = float(value_max)
         self.dtype = name

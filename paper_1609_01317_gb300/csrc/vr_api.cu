@@ -471,6 +471,7 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
   if (!(value_max > 0.0f) || !std::isfinite(value_max)) return VR_ERR_INVALID_ARG;
   const int eb = dtype_bytes(dtype);
   if (eb == 0) return VR_ERR_UNSUPPORTED;
+  if (!aligned_to(voxels, (size_t)eb)) return VR_ERR_INVALID_ARG;
   const long long nvox = (long long)nx * ny * nz;
   // x pitch: a multiple of 16 elements and at least nx + 8, so that the vector row loads
   // of the brick footprints (which start at padded x = 8 bx) stay inside each row
@@ -609,6 +610,7 @@ vr_status vr_render(vr_ctx* ctx, const vr_render_params* params, float* out_rgba
   const size_t bytes = (size_t)ctx->cam.width * ctx->cam.height * sizeof(float4);
   float* dst = out_rgba;
   const bool host_out = !is_device_pointer(out_rgba);
+  if (!host_out && !aligned_to(out_rgba, 16)) return VR_ERR_INVALID_ARG;
   if (host_out) {
     st = ensure(ctx, &ctx->out_staging, &ctx->out_cap, bytes);
     if (st != VR_OK) return st;
@@ -648,6 +650,7 @@ vr_status vr_render_forward_train(vr_ctx* ctx, const vr_render_params* params, f
   DeviceGuard g(ctx->device);
   if (!g.ok) return cuda_status(cudaGetLastError());
   if (!is_device_pointer(out_rgba) || !is_device_pointer(checkpoints)) return VR_ERR_INVALID_ARG;
+  if (!aligned_to(out_rgba, 16)) return VR_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* kend = static_cast<int*>(checkpoints);
   float* Tend = reinterpret_cast<float*>(static_cast<char*>(checkpoints) + align256((size_t)nrays * 4));
@@ -704,9 +707,12 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
   DeviceGuard g(ctx->device);
   if (!g.ok) return cuda_status(cudaGetLastError());
   for (int v = 0; v < nviews; ++v)
-    if (!is_device_pointer(grad_rgba[v])) return VR_ERR_INVALID_ARG;
-  if (grad_volume && !is_device_pointer(grad_volume)) return VR_ERR_INVALID_ARG;
-  if (grad_tf && !is_device_pointer(grad_tf)) return VR_ERR_INVALID_ARG;
+    if (!is_device_pointer(grad_rgba[v]) || !aligned_to(grad_rgba[v], 16))
+      return VR_ERR_INVALID_ARG;
+  if (grad_volume && (!is_device_pointer(grad_volume) || !aligned_to(grad_volume, 4)))
+    return VR_ERR_INVALID_ARG;
+  if (grad_tf && (!is_device_pointer(grad_tf) || !aligned_to(grad_tf, 4)))
+    return VR_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t nvox = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
   if (grad_volume) {

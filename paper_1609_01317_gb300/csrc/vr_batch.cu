@@ -210,7 +210,7 @@ vr_status vr_batch_create(vr_batch** out, vr_ctx* const* ctxs, int nctx, const v
     }
   } restore{prev, dev};
   for (int i = 0; i < ncams; ++i)
-    if (!is_device_pointer(outs[i])) return VR_ERR_INVALID_ARG;
+    if (!is_device_pointer(outs[i]) || !aligned_to(outs[i], 16)) return VR_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // gradient records of every volume (computed on `stream` if out of date)
   for (int i = 0; i < nctx; ++i) {
@@ -380,7 +380,7 @@ vr_status vr_render_batch(vr_ctx* const* vols, const vr_camera* cams, const int*
     }
   } restore{prev, owner->device};
   for (int i = 0; i < n; ++i)
-    if (!is_device_pointer(outs[i])) return VR_ERR_INVALID_ARG;
+    if (!is_device_pointer(outs[i]) || !aligned_to(outs[i], 16)) return VR_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < nvol; ++i) {
     st = ensure_records(vols[i], params, s);

@@ -127,6 +127,12 @@ vr_status check_params(const vr_render_params* p);
 vr_status check_camera(const vr_camera* cam, CamDev* basis);
 bool camera_basis(const vr_camera* c, CamDev* b);
 bool is_device_pointer(const void* p);
+// whether p is a multiple of `bytes` (a power of two): device buffers the kernels access as
+// float4 (images, image gradients, a transfer function read in place) need 16, other float
+// buffers 4, voxel arrays their element size
+inline bool aligned_to(const void* p, size_t bytes) {
+  return (reinterpret_cast<uintptr_t>(p) & (bytes - 1)) == 0;
+}
 
 // device descriptors
 VolDev vol_dev(const vr_ctx* ctx);

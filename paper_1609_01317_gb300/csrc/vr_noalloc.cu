@@ -215,6 +215,10 @@ extern "C" vr_status vr_render_noalloc(const void* voxels, vr_dtype dtype, int n
   if (!(value_max > 0.0f) || !(value_max < 3.0e38f)) return VR_ERR_INVALID_ARG;
   if (dtype != VR_U8 && dtype != VR_U16 && dtype != VR_F16 && dtype != VR_F32)
     return VR_ERR_UNSUPPORTED;
+  // the kernels read the table and write the image as float4 and read voxels as elements
+  const size_t esz = dtype == VR_U8 ? 1 : (dtype == VR_F32 ? 4 : 2);
+  if (!aligned_to(voxels, esz) || !aligned_to(tf_rgba, 16) || !aligned_to(out_rgba, 16))
+    return VR_ERR_INVALID_ARG;
   if ((long long)nx * ny * nz > 2147483647LL) return VR_ERR_INVALID_ARG;
   const int nb[3] = {(nx + kBrick - 1) / kBrick, (ny + kBrick - 1) / kBrick,
                      (nz + kBrick - 1) / kBrick};

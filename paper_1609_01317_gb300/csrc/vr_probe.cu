@@ -68,6 +68,7 @@ vr_status vr_probe_samples(vr_ctx* ctx, const vr_render_params* params, const fl
   if (params->adaptive) return VR_ERR_UNSUPPORTED;
   if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
   if (!is_device_pointer(pos) || !is_device_pointer(out)) return VR_ERR_INVALID_ARG;
+  if (!aligned_to(pos, 4) || !aligned_to(out, 4)) return VR_ERR_INVALID_ARG;
   if (n == 0) return VR_OK;
   int prev = -1;
   cudaGetDevice(&prev);

@@ -235,6 +235,9 @@ extern "C" vr_status vr_render_surface(vr_ctx* ctx, const vr_surface_params* par
   const size_t npix = (size_t)ctx->cam.width * ctx->cam.height;
   const bool host_rgba = !is_device_pointer(out_rgba);
   const bool host_depth = out_depth && !is_device_pointer(out_depth);
+  if ((!host_rgba && !aligned_to(out_rgba, 16)) ||
+      (out_depth && !host_depth && !aligned_to(out_depth, 4)))
+    return VR_ERR_INVALID_ARG;
   // device staging for host outputs: image, then depth
   const size_t img_bytes = npix * sizeof(float4), depth_bytes = npix * sizeof(float);
   if (host_rgba || host_depth) {

@@ -144,6 +144,46 @@ def _ptr(x):
     raise TypeError(f"cannot take the address of {type(x)}")
 
 
+# ------------------------------------------------------------- buffer checks
+# What the binding knows of each context (image size of the camera, voxel count, table
+# entries), so that buffers handed to a call can be checked against what the call touches.
+_state = {}
+_ELEM = {0: 1, 1: 2, 2: 2, 3: 4}  # bytes per voxel of each vr_dtype
+
+
+def _buf(func, x, nbytes, elem=None, device_only=False, what="buffer"):
+    """Check a torch tensor or numpy array handed to `func`: contiguous, at least `nbytes`
+    long, elements of `elem` bytes (when given) and, for `device_only` arguments, CUDA
+    memory.  Raises VrError(VR_ERR_INVALID_ARG) before the library is called.  Raw integer
+    addresses and None pass unchecked (the library validates what it can)."""
+    if x is None or isinstance(x, int):
+        return
+    if hasattr(x, "data_ptr") and hasattr(x, "is_contiguous"):
+        if not x.is_contiguous():
+            raise VrError(func, 1, f"{what} is not contiguous")
+        if device_only and not x.is_cuda:
+            raise VrError(func, 1, f"{what} must be CUDA device memory")
+        es, have = x.element_size(), x.numel() * x.element_size()
+    elif hasattr(x, "ctypes") and hasattr(x, "flags"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise VrError(func, 1, f"{what} is not C-contiguous")
+        if device_only:
+            raise VrError(func, 1, f"{what} must be CUDA device memory, not a numpy array")
+        es, have = x.itemsize, x.nbytes
+    else:
+        return
+    if elem is not None and es != elem:
+        raise VrError(func, 1, f"{what} has {es}-byte elements, {elem} expected")
+    if have < nbytes:
+        raise VrError(func, 1, f"{what} holds {have} bytes, the call touches {nbytes}")
+
+
+def _image_bytes(cam) -> int:
+    if isinstance(cam, vr_camera):
+        return int(cam.width) * int(cam.height) * 16
+    return int(cam["width"]) * int(cam["height"]) * 16
+
+
 def make_camera(cam: dict) -> vr_camera:
     return vr_camera((C.c_float * 3)(*cam["eye"]), (C.c_float * 3)(*cam["target"]),
                      (C.c_float * 3)(*cam["up"]), int(bool(cam["ortho"])),
@@ -183,30 +223,39 @@ def vr_create(device=0, alloc=None, free=None, user=None):
     a = alloc if alloc is not None else ALLOC_FN()
     f = free if free is not None else FREE_FN()
     _check("vr_create", lib().vr_create(C.byref(h), int(device), a, f, user))
+    _state[h.value] = {}
     return h.value
 
 
 def vr_destroy(ctx):
+    _state.pop(ctx, None)
     lib().vr_destroy(ctx)
 
 
 def vr_upload_volume(ctx, voxels, dtype, nx, ny, nz, value_max, stream=None):
     dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    nvox = int(nx) * int(ny) * int(nz)
+    _buf("vr_upload_volume", voxels, nvox * _ELEM.get(dt, 1), _ELEM.get(dt), what="voxels")
     _check("vr_upload_volume", lib().vr_upload_volume(ctx, _ptr(voxels), dt, int(nx), int(ny),
                                                       int(nz), float(value_max), stream))
+    _state.setdefault(ctx, {})["nvox"] = nvox
 
 
 def vr_set_transfer_function(ctx, rgba, n, stream=None):
+    _buf("vr_set_transfer_function", rgba, int(n) * 16, 4, what="rgba")
     _check("vr_set_transfer_function", lib().vr_set_transfer_function(ctx, _ptr(rgba), int(n),
                                                                       stream))
+    _state.setdefault(ctx, {})["ntf"] = int(n)
 
 
 def vr_set_camera(ctx, cam):
     c = cam if isinstance(cam, vr_camera) else make_camera(cam)
     _check("vr_set_camera", lib().vr_set_camera(ctx, C.byref(c)))
+    _state.setdefault(ctx, {})["image"] = _image_bytes(c)
 
 
 def vr_render(ctx, params, out_rgba, stream=None):
+    _buf("vr_render", out_rgba, _state.get(ctx, {}).get("image", 0), 4, what="out_rgba")
     _check("vr_render", lib().vr_render(ctx, C.byref(params), _ptr(out_rgba), stream))
 
 
@@ -217,12 +266,19 @@ def vr_checkpoint_bytes(ctx, params) -> int:
 
 
 def vr_render_forward_train(ctx, params, out_rgba, checkpoints, checkpoint_bytes, stream=None):
+    _buf("vr_render_forward_train", out_rgba, _state.get(ctx, {}).get("image", 0), 4, True,
+         "out_rgba")
+    _buf("vr_render_forward_train", checkpoints, int(checkpoint_bytes), None, True, "checkpoints")
     _check("vr_render_forward_train",
            lib().vr_render_forward_train(ctx, C.byref(params), _ptr(out_rgba), _ptr(checkpoints),
                                          int(checkpoint_bytes), stream))
 
 
 def vr_render_backward(ctx, params, checkpoints, grad_rgba, grad_volume, grad_tf, stream=None):
+    st = _state.get(ctx, {})
+    _buf("vr_render_backward", grad_rgba, st.get("image", 0), 4, True, "grad_rgba")
+    _buf("vr_render_backward", grad_volume, 4 * st.get("nvox", 0), 4, True, "grad_volume")
+    _buf("vr_render_backward", grad_tf, 16 * st.get("ntf", 0), 4, True, "grad_tf")
     _check("vr_render_backward",
            lib().vr_render_backward(ctx, C.byref(params), _ptr(checkpoints), _ptr(grad_rgba),
                                     _ptr(grad_volume), _ptr(grad_tf), stream))
@@ -232,6 +288,10 @@ def vr_render_noalloc(voxels, dtype, nx, ny, nz, value_max, tf_rgba, ntf, cam, p
                       out_rgba, stream=None):
     dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     c = cam if isinstance(cam, vr_camera) else make_camera(cam)
+    f = "vr_render_noalloc"
+    _buf(f, voxels, int(nx) * int(ny) * int(nz) * _ELEM.get(dt, 1), _ELEM.get(dt), True, "voxels")
+    _buf(f, tf_rgba, int(ntf) * 16, 4, True, "tf_rgba")
+    _buf(f, out_rgba, _image_bytes(c), 4, True, "out_rgba")
     _check("vr_render_noalloc",
            lib().vr_render_noalloc(_ptr(voxels), dt, int(nx), int(ny), int(nz), float(value_max),
                                    _ptr(tf_rgba), int(ntf), C.byref(c), C.byref(params),
@@ -242,6 +302,11 @@ def vr_render_backward_views(ctx, params, cams, checkpoints, grad_rgbas, grad_vo
                              stream=None):
     n = len(cams)
     carr = (vr_camera * n)(*[c if isinstance(c, vr_camera) else make_camera(c) for c in cams])
+    st = _state.get(ctx, {})
+    for c, g in zip(carr, grad_rgbas):
+        _buf("vr_render_backward_views", g, _image_bytes(c), 4, True, "grad_rgba")
+    _buf("vr_render_backward_views", grad_volume, 4 * st.get("nvox", 0), 4, True, "grad_volume")
+    _buf("vr_render_backward_views", grad_tf, 16 * st.get("ntf", 0), 4, True, "grad_tf")
     karr = (C.c_void_p * n)(*[_ptr(k) for k in checkpoints])
     garr = (C.c_void_p * n)(*[_ptr(g) for g in grad_rgbas])
     _check("vr_render_backward_views",
@@ -260,6 +325,8 @@ def vr_batch_create(ctxs, cams, ctx_of_cam, params, outs, stream=None):
     h = C.c_void_p()
     carr = (C.c_void_p * len(ctxs))(*ctxs)
     cams_arr = (vr_camera * n)(*[c if isinstance(c, vr_camera) else make_camera(c) for c in cams])
+    for c, o in zip(cams_arr, outs):
+        _buf("vr_batch_create", o, _image_bytes(c), 4, True, "outs[i]")
     idx = (C.c_int * n)(*[int(i) for i in ctx_of_cam])
     oarr = (C.c_void_p * n)(*[_ptr(o) for o in outs])
     _check("vr_batch_create", lib().vr_batch_create(C.byref(h), carr, len(ctxs), cams_arr, idx, n,
@@ -282,6 +349,9 @@ def vr_batch_destroy(batch):
 
 
 def vr_render_surface(ctx, params, out_rgba, out_depth=None, stream=None):
+    img = _state.get(ctx, {}).get("image", 0)
+    _buf("vr_render_surface", out_rgba, img, 4, what="out_rgba")
+    _buf("vr_render_surface", out_depth, img // 4, 4, what="out_depth")
     _check("vr_render_surface", lib().vr_render_surface(ctx, C.byref(params), _ptr(out_rgba),
                                                         _ptr(out_depth), stream))
 
@@ -290,6 +360,8 @@ def vr_render_batch(vols, cams, vol_of_cam, params, outs, stream=None):
     n = len(cams)
     varr = (C.c_void_p * len(vols))(*vols)
     cams_arr = (vr_camera * n)(*[c if isinstance(c, vr_camera) else make_camera(c) for c in cams])
+    for c, o in zip(cams_arr, outs):
+        _buf("vr_render_batch", o, _image_bytes(c), 4, True, "outs[i]")
     idx = (C.c_int * n)(*[int(i) for i in vol_of_cam])
     oarr = (C.c_void_p * n)(*[_ptr(o) for o in outs])
     _check("vr_render_batch", lib().vr_render_batch(varr, cams_arr, idx, n, C.byref(params), oarr,
@@ -306,6 +378,8 @@ def vr_screen_rect(cam, lo, hi):
 
 
 def vr_probe_samples(ctx, params, pos, n, out, stream=None):
+    _buf("vr_probe_samples", pos, 12 * max(int(n), 0), 4, True, "pos")
+    _buf("vr_probe_samples", out, 48 * max(int(n), 0), 4, True, "out")
     _check("vr_probe_samples", lib().vr_probe_samples(ctx, C.byref(params), _ptr(pos), int(n),
                                                       _ptr(out), stream))
 

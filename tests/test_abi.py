@@ -106,3 +106,34 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 0 and "raised" in r.stdout and "missing" in r.stdout
+
+
+def test_binding_checks_buffers_before_calling_the_library(libvr):
+    """The binding rejects a non-contiguous, short, wrongly typed or host-resident buffer
+    with VR_ERR_INVALID_ARG before the library (or a GPU) is touched."""
+    import numpy as np
+    import torch
+
+    from paper_1609_01317_gb300 import vr
+
+    cam = {"eye": [0, 0, 40], "target": [0, 0, 0], "up": [0, 1, 0], "ortho": 0,
+           "fov_y_deg": 40.0, "ortho_height": 1.0, "width": 8, "height": 6}
+    p = vr.make_params()
+
+    def rejected(fn, *a):
+        with pytest.raises(vr.VrError) as e:
+            fn(*a)
+        assert e.value.status == 1
+
+    # transposed (non-contiguous) image
+    rejected(vr.vr_render, None, p, torch.zeros(6, 8, 4).transpose(0, 1))
+    # voxels: too few bytes for 4 x 4 x 4 u16, and u16 voxels given as float32
+    rejected(vr.vr_upload_volume, None, np.zeros(60, np.uint16), "u16", 4, 4, 4, 4095.0)
+    rejected(vr.vr_upload_volume, None, np.zeros(64, np.float32), "u16", 4, 4, 4, 4095.0)
+    # transfer function shorter than n entries
+    rejected(vr.vr_set_transfer_function, None, np.zeros((3, 4), np.float32), 4)
+    # the allocation-free render takes device memory only, and whole images
+    rejected(vr.vr_render_noalloc, np.zeros(64, np.uint8), "u8", 4, 4, 4, 255.0,
+             np.zeros((2, 4), np.float32), 2, cam, p, np.zeros((6, 8, 4), np.float32))
+    # probe points: 3 floats per point
+    rejected(vr.vr_probe_samples, None, p, torch.zeros(5), 2, torch.zeros(24))
