@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--workload", choices=["ct", "ellipsoids", "sphere"], default="ct")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch", "surface", "adaptive"],
+    ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch", "surface", "adaptive", "train",
+                                      "f16"],
                     default="main",
                     help="run one leg alone and print its JSON (for profiling)")
     ap.add_argument("--source-hash", choices=sorted(KERNEL_SOURCES),
@@ -398,17 +399,51 @@ def batch_leg(args):
     reps = max(3, min(args.steps, 5))
     t_b = timed(batched, reps)
     t_s = timed(separate, reps)
+    # sampled pixels of every batched render (48 whose ray reaches something, 16 anywhere),
+    # kept for the comparison with the FP64 oracle in the CPU-baseline leg
+    batched()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(2024)
+    picks, got = [], []
+    for o in outs:
+        hit = torch.nonzero(o[..., 3] > 0).cpu().numpy()
+        sel = hit[rng.choice(len(hit), size=min(48, len(hit)), replace=False)] if len(hit) else \
+            np.zeros((0, 2), np.int64)
+        yx = np.concatenate([sel, np.stack([rng.integers(0, o.shape[0], 16),
+                                            rng.integers(0, o.shape[1], 16)], 1)]).astype(np.int32)
+        px, py = yx[:, 1].copy(), yx[:, 0].copy()
+        picks.append((px, py))
+        got.append(o[torch.from_numpy(py).long().cuda(), torch.from_numpy(px).long().cuda()]
+                   .cpu().numpy())
     vr.vr_batch_destroy(b)
     for r in rends:
         r.close()
     n = len(cams)
-    return {"workload": f"batch8vol_{n}renders_512_cd", "renders": n, "samples": samples,
+    return {"_samples": {"wl": wl, "cams": cams, "owner": owner, "picks": picks, "got": got},
+            "workload": f"batch8vol_{n}renders_512_cd", "renders": n, "samples": samples,
             "volume_scale": args.batch_scale, "autotuned": {"threads": chosen[0],
                                                             "tile": [chosen[1], chosen[2]]},
             "batched_ms": t_b, "separate_ms": t_s, "speedup": t_s / t_b,
             "batched_gsamples_s": samples / (t_b / 1e3) / 1e9,
             "separate_gsamples_s": samples / (t_s / 1e3) / 1e9,
             "renders_per_s": n / (t_b / 1e3), "phantom_generation_s": gen_s}
+
+
+def batch_parity(bs):
+    """The batched renders' sampled pixels against the FP64 oracle's rays through the same
+    pixels (per-pixel max abs over RGBA)."""
+    import oracle
+
+    pr = oracle.make_params(grad="central")
+    ovs = [oracle.OracleVolume(w["volume"], w["value_max"]) for w in bs["wl"]]
+    errs = []
+    for c, o, (px, py), g in zip(bs["cams"], bs["owner"], bs["picks"], bs["got"]):
+        ref, _, _ = oracle.render_pixels(ovs[o], bs["wl"][o]["tf"], c, pr, px, py)
+        errs.append(np.abs(g.astype(np.float64) - ref).max(axis=-1))
+    e = np.concatenate(errs)
+    return {"reference": "FP64 oracle", "renders": len(errs), "pixels": int(e.size),
+            "sample": "48 pixels whose ray reaches something + 16 anywhere, per render",
+            "max_abs": float(e.max()), "frac_within_2e-3": float((e <= 2e-3).mean())}
 
 
 def surface_leg(R, args):
@@ -572,6 +607,150 @@ def fwd_bwd_leg(R, args):
             "fwd_bwd_gsamples_s": samples / (t_fb / 1e3) / 1e9}
 
 
+def train_leg(R, args, steps=200):
+    """Differentiable workload trained: a learnable 128^3 float32 density (blurred random
+    field, seed 4) and 256-entry TF (the sphere workload's ramp) fitted by Adam (lr 1e-2) to
+    16 views at 256 x 256 of the hidden 128^3 ellipsoid phantom (seed 3), L2 image loss,
+    central differences, termination at 0.99.  One step = upload volume + set TF + 16
+    checkpointed forwards + the adjoint of all 16 views + the Adam update (torch on the
+    device), no host synchronisation inside the loop.  Gsamples/s counts the plain-method
+    samples of every forward (the sum of the rays' recorded end indices)."""
+    import torch
+
+    import phantoms as P
+    from paper_1609_01317_gb300 import vr
+
+    n, H, W = 128, 256, 256
+    dev = "cuda"
+    ctx = R.ctx
+    sh = torch.cuda.current_stream().cuda_stream or None
+    views = P.training_views(n, W, H)
+    cams = [vr.make_camera(c) for c in views]
+    params = vr.make_params(grad="central", skip_empty=False, ert_threshold=0.99)
+    tf0 = torch.from_numpy(P.tf_c1(256)).to(dev)
+    hidden = torch.from_numpy(P.density_phantom(3, n)).to(dev)
+    vr.vr_upload_volume(ctx, hidden, "f32", n, n, n, 1.0, sh)
+    vr.vr_set_transfer_function(ctx, tf0, 256, sh)
+    targets = []
+    for c in cams:
+        vr.vr_set_camera(ctx, c)
+        t = torch.empty((H, W, 4), device=dev)
+        vr.vr_render(ctx, params, t, sh)
+        targets.append(t)
+    vol = torch.from_numpy(P.blurred_random_field(4, n)).to(dev)
+    tf = tf0.clone()
+    opt = torch.optim.Adam([vol.requires_grad_(), tf.requires_grad_()], lr=1e-2)
+    vr.vr_set_camera(ctx, cams[0])
+    nb = vr.vr_checkpoint_bytes(ctx, params)
+    ck = [torch.empty(nb + 256, dtype=torch.uint8, device=dev) for _ in cams]
+    ckv = [c[(-c.data_ptr()) % 256:][:nb] for c in ck]
+    imgs = [torch.empty((H, W, 4), device=dev) for _ in cams]
+    gimgs = [torch.empty((H, W, 4), device=dev) for _ in cams]
+    gv = torch.zeros_like(vol)
+    gt = torch.zeros_like(tf)
+    loss = torch.zeros((), device=dev, dtype=torch.float64)
+    samples = torch.zeros((), device=dev, dtype=torch.int64)
+    norm = 1.0 / (len(cams) * H * W * 4)
+
+    def step():
+        vr.vr_upload_volume(ctx, vol.detach(), "f32", n, n, n, 1.0, sh)
+        vr.vr_set_transfer_function(ctx, tf.detach(), 256, sh)
+        loss.zero_()
+        for i, c in enumerate(cams):
+            vr.vr_set_camera(ctx, c)
+            vr.vr_render_forward_train(ctx, params, imgs[i], ckv[i], nb, sh)
+            d = imgs[i] - targets[i]
+            loss.add_((d * d).sum(dtype=torch.float64) * norm)
+            torch.mul(d, 2.0 * norm, out=gimgs[i])
+            samples.add_(ckv[i][:4 * H * W].view(torch.int32).sum())
+        gv.zero_()
+        gt.zero_()
+        vr.vr_render_backward_views(ctx, params, cams, ckv, gimgs, gv, gt, sh)
+        vol.grad, tf.grad = gv, gt
+        opt.step()
+        with torch.no_grad():
+            vol.clamp_(0.0, 1.0)
+            tf.clamp_(0.0, 1.0)
+
+    step()  # the first step, untimed (lazy Adam state)
+    first = float(loss.item())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    samples.zero_()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps - 1):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (steps - 1)
+    total = int(samples.item())
+    vr.vr_upload_volume(ctx, vol.detach(), "f32", n, n, n, 1.0, sh)
+    vr.vr_set_transfer_function(ctx, tf.detach(), 256, sh)
+    final = 0.0
+    for i, c in enumerate(cams):  # loss of the trained state
+        vr.vr_set_camera(ctx, c)
+        vr.vr_render(ctx, params, imgs[i], sh)
+        final += float(((imgs[i] - targets[i]) ** 2).sum(dtype=torch.float64)) * norm
+    return {"workload": "density128_f32_16views256_cd_adam", "adam_steps": steps,
+            "lr": 1e-2, "ms_per_step": ms,
+            "fwd_bwd_gsamples_s": total / ((steps - 1) * ms / 1e3) / 1e9,
+            "samples_per_step": total / (steps - 1), "loss_first": first, "loss_final": final,
+            "timed": f"{steps - 1} steps after the first (CUDA events, no host sync inside)"}
+
+
+def f16_leg(args, K):
+    """The CT frame with the volume stored as FP16 (raw / 4095, value_max 1), timed as the
+    main step (upload + TF + camera + render).  Returns the leg's dict, the image and the
+    volume (for the oracle comparison in the CPU-baseline leg)."""
+    import torch
+
+    import phantoms as P
+    from paper_1609_01317_gb300 import Renderer, vr
+
+    w = P.workload_ct()
+    v16 = (w["volume"].astype(np.float32) / np.float32(4095.0)).astype(np.float16)
+    nz, ny, nx = v16.shape
+    cam = w["camera"]
+    H, W = cam["height"], cam["width"]
+    R = Renderer(torch.cuda.current_device())
+    ctx = R.ctx
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream or None
+    vdev = torch.from_numpy(v16).cuda()
+    tdev = torch.from_numpy(w["tf"]).cuda()
+    out = torch.empty((H, W, 4), device="cuda")
+    params = vr.make_params(step=w["step"], grad=w["grad"], skip_empty=w["skip_empty"])
+    cam_s = vr.make_camera(cam)
+
+    def step(p=params):
+        vr.vr_upload_volume(ctx, vdev, "f16", nx, ny, nz, 1.0, sh)
+        vr.vr_set_transfer_function(ctx, tdev, tdev.shape[0], sh)
+        vr.vr_set_camera(ctx, cam_s)
+        vr.vr_render(ctx, p, out, sh)
+
+    step(vr.make_params(step=w["step"], grad=w["grad"], skip_empty=w["skip_empty"],
+                        collect_stats=True))
+    st = vr.vr_read_stats(ctx, sh)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        step()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    for i in range(K):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    img = out.cpu().numpy()
+    R.close()
+    return ({"workload": "ct512x512x361_f16_persp1920x1080_zh", "storage": "f16 = raw / 4095",
+             "ms_per_step": ms, "value": st["samples_plain"] / (ms / 1e3) / 1e9,
+             "unit": "Gsamples/s", "samples_per_frame": st["samples_plain"],
+             "samples_visited": st["samples_visited"], "samples_shaded": st["samples_shaded"]},
+            img, v16)
+
+
 def run_ours(args):
     import torch
 
@@ -712,7 +891,10 @@ def run_ours(args):
     }
     line["clocks"] = clk.summary()
 
+    f16_img = f16_vol = None
     if not args.no_extras:
+        line["f16"], f16_img, f16_vol = f16_leg(args, max(10, min(K, 50)))
+        line["train"] = train_leg(R, args)
         line["fwd_bwd"] = fwd_bwd_leg(R, args)
         line["surface"] = surface_leg(R, args)
         line["adaptive"] = adaptive_leg(R, args)
@@ -813,6 +995,23 @@ def run_ours(args):
                           "pixels": int(err.size), "max_abs": float(err.max()),
                           "frac_within_2e-3": float((err <= 2e-3).mean()),
                           "mean_abs": float(np.abs(gpu - ref).mean())}
+        if f16_img is not None:
+            # the FP16 frame against the FP64 oracle's frame of the same FP16 volume, whole
+            # image (both storage variants' errors side by side)
+            import oracle
+
+            t0 = time.perf_counter()
+            ref16, _, _ = oracle.render(oracle.OracleVolume(f16_vol, 1.0), w["tf"], cam,
+                                        oracle.make_params(step=w["step"], grad=w["grad"]))
+            e16 = np.abs(f16_img.astype(np.float64) - ref16).max(axis=-1)
+            line["f16"]["parity"] = {"reference": "FP64 oracle", "rows": [0, H],
+                                     "pixels": int(e16.size), "max_abs": float(e16.max()),
+                                     "frac_within_2e-3": float((e16 <= 2e-3).mean()),
+                                     "mean_abs": float(np.abs(f16_img - ref16).mean()),
+                                     "oracle_s": time.perf_counter() - t0}
+        bs = line.get("batch", {}).pop("_samples", None)
+        if bs is not None:
+            line["batch"]["parity"] = batch_parity(bs)
         line["cpu_baseline"] = {"value": cb["samples"] / cb["seconds"] / 1e9,
                                 "unit": "Gsamples/s", "cores": cb["cores"], "kind": "oracle",
                                 "sample": f"{what} of the workload "
@@ -822,6 +1021,8 @@ def run_ours(args):
     else:
         line["e2e"] = None
         line["cpu_baseline"] = None
+    if isinstance(line.get("batch"), dict):
+        line["batch"].pop("_samples", None)  # host copies kept only for the oracle comparison
     if rank == 0:
         print(json.dumps(line), flush=True)
     R.close()
@@ -839,13 +1040,16 @@ def run_leg(args):
 
     build.build()
     torch.cuda.set_device(0)
-    if args.leg in ("fwd_bwd", "surface", "adaptive"):
+    if args.leg in ("fwd_bwd", "surface", "adaptive", "train"):
         R = Renderer(0)
-        out = {"fwd_bwd": fwd_bwd_leg, "surface": surface_leg,
-               "adaptive": adaptive_leg}[args.leg](R, args)
+        out = {"fwd_bwd": fwd_bwd_leg, "surface": surface_leg, "adaptive": adaptive_leg,
+               "train": train_leg}[args.leg](R, args)
         R.close()
+    elif args.leg == "f16":
+        out = f16_leg(args, max(10, min(args.steps, 50)))[0]
     else:
         out = batch_leg(args)
+        out.pop("_samples", None)
     print(json.dumps(out), flush=True)
     return 0
 

@@ -176,8 +176,11 @@ vr_status vr_checkpoint_bytes(vr_ctx *ctx, const vr_render_params *params, size_
 
 /* vr_render that also records, in the caller-owned device buffer `checkpoints` (at least
  * vr_checkpoint_bytes bytes, 256-byte aligned), what vr_render_backward needs: each ray's
- * end index and its transmittance before every 32nd sample.  out_rgba must be device
- * memory.  Errors as vr_render, plus INVALID_ARG for a short or unaligned buffer. */
+ * end index and its transmittance before every 32nd sample.  The buffer begins with the
+ * end indices: int32, one per pixel in image order (row-major), each the number of samples
+ * the ray marched up to and including the one that terminated it (its sample count K when
+ * it did not terminate).  out_rgba must be device memory.  Errors as vr_render, plus
+ * INVALID_ARG for a short or unaligned buffer. */
 vr_status vr_render_forward_train(vr_ctx *ctx, const vr_render_params *params,
                                   float *out_rgba, void *checkpoints, size_t checkpoint_bytes,
                                   void *stream);
