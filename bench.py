@@ -52,13 +52,16 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch", "surface", "adaptive", "train",
-                                      "f16"],
+                                      "f16", "sparse"],
                     default="main",
                     help="run one leg alone and print its JSON (for profiling)")
     ap.add_argument("--source-hash", choices=sorted(KERNEL_SOURCES),
                     help="print the source hash recorded beside a kernel's ncu counters")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="edge scale of the batched-render volumes (1.0 = full sizes)")
+    ap.add_argument("--mode", choices=["replicas", "sortfirst"], default="replicas",
+                    help="N > 1: independent replicas of the frame (weak scaling, default) or "
+                         "one frame split by rows over the ranks and gathered (strong)")
     return ap.parse_args()
 
 
@@ -751,11 +754,156 @@ def f16_leg(args, K):
             img, v16)
 
 
+def sparse_leg(args, K):
+    """The sparse workload of the skipping hierarchy (§5.4): a 512^3 uint16 vessel tree in
+    empty space rendered at 3840 x 2160 (Zucker-Hummel, step 0.5, skipping + termination).
+    Times the whole step (upload + TF + camera + render) and the render alone; keeps sampled
+    pixels for the oracle comparison in the CPU-baseline leg."""
+    import torch
+
+    import phantoms as P
+    from paper_1609_01317_gb300 import Renderer, vr
+
+    w = P.workload_sparse()
+    vol = w["volume"]
+    nz, ny, nx = vol.shape
+    cam = w["camera"]
+    H, W = cam["height"], cam["width"]
+    R = Renderer(torch.cuda.current_device())
+    ctx = R.ctx
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream or None
+    vdev = torch.from_numpy(vol.view(np.int16)).cuda()
+    tdev = torch.from_numpy(w["tf"]).cuda()
+    out = torch.empty((H, W, 4), device="cuda")
+    params = vr.make_params(step=w["step"], grad=w["grad"], skip_empty=True)
+    cam_s = vr.make_camera(cam)
+
+    def step(p=params):
+        vr.vr_upload_volume(ctx, vdev, "u16", nx, ny, nz, w["value_max"], sh)
+        vr.vr_set_transfer_function(ctx, tdev, tdev.shape[0], sh)
+        vr.vr_set_camera(ctx, cam_s)
+        vr.vr_render(ctx, p, out, sh)
+
+    step(vr.make_params(step=w["step"], grad=w["grad"], skip_empty=True, collect_stats=True))
+    st = vr.vr_read_stats(ctx, sh)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        step()
+
+    def timed(fn):
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+        for i in range(K):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    step_ms = timed(step)
+    render_ms = timed(lambda: vr.vr_render(ctx, params, out, sh))
+    img = out
+    hit = torch.nonzero(img[..., 3] > 0).cpu().numpy()
+    rng = np.random.default_rng(9)
+    pick = np.concatenate([hit[rng.choice(len(hit), min(1500, len(hit)), replace=False)],
+                           rng.integers(0, [H, W], size=(300, 2))])
+    got = img[torch.from_numpy(pick[:, 0]).cuda(), torch.from_numpy(pick[:, 1]).cuda()].cpu().numpy()
+    R.close()
+    return {"_samples": {"w": w, "pick": pick, "got": got},
+            "workload": w["name"], "ms_per_step": step_ms, "render_ms": render_ms,
+            "value": st["samples_plain"] / (step_ms / 1e3) / 1e9, "unit": "Gsamples/s",
+            "render_gsamples_s": st["samples_plain"] / (render_ms / 1e3) / 1e9,
+            "samples_per_frame": st["samples_plain"], "samples_visited": st["samples_visited"],
+            "samples_shaded": st["samples_shaded"], "rays_hit": st["rays_hit"],
+            "voxels_nonzero_frac": float((vol > 0).mean())}
+
+
+def run_sortfirst(args):
+    """One frame of the workload split by rows over the ranks (sort-first, §2.2: rays are
+    independent): every rank uploads the volume and renders its band of the busy rows
+    (vr_render_rows), the bands are all-gathered over NCCL and stitched into the frame on
+    every rank.  Strong scaling: value = the frame's plain samples / the slowest rank's
+    step time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1609_01317_gb300 import Renderer, build, sortfirst as SF, vr
+
+    rank, world, local = dist_setup(args)
+    build.build()
+    w = workload(args.workload)
+    vol = w["volume"]
+    nz, ny, nx = vol.shape
+    dt = dtype_name(vol)
+    cam = w["camera"]
+    H, W = cam["height"], cam["width"]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream or None
+    vol_dev = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
+    tf_dev = torch.from_numpy(w["tf"]).cuda()
+    R = Renderer(local)
+    ctx = R.ctx
+    params = vr.make_params(step=w["step"], grad=w["grad"], skip_empty=w["skip_empty"])
+    cam_s = vr.make_camera(cam)
+    busy = vr.vr_screen_rect(cam, (0.0, 0.0, 0.0), (nx - 1.0, ny - 1.0, nz - 1.0))
+    part = SF.RowPartition.from_bands(H, W, world, busy=(busy[1], busy[3]))
+    packed = torch.zeros((part.capacity, W, 4), device="cuda")
+    frame = torch.empty((H, W, 4), device="cuda")
+
+    def render_rows(a, b, dst, p=params):
+        vr.vr_render_rows(ctx, p, a, b, dst, sh)
+
+    def step(p=params):
+        vr.vr_upload_volume(ctx, vol_dev, dt, nx, ny, nz, w["value_max"], sh)
+        vr.vr_set_transfer_function(ctx, tf_dev, tf_dev.shape[0], sh)
+        vr.vr_set_camera(ctx, cam_s)
+        part.render_local(rank, lambda a, b, dst: render_rows(a, b, dst, p), packed)
+        part.gather(packed, frame)
+
+    pst = vr.make_params(step=w["step"], grad=w["grad"], skip_empty=w["skip_empty"],
+                         collect_stats=True)
+    step(pst)
+    mine = vr.vr_read_stats(ctx, sh)["samples_plain"] if part.per_rank[rank] else 0
+    samples = int(sum_over_ranks(float(mine), world))
+    for _ in range(args.warmup):
+        step()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for i in range(K):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        barrier(world)
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+    ms = total_ms / K
+    line = {"metric": "Gsamples/s", "value": samples / (ms / 1e3) / 1e9, "unit": "Gsamples/s",
+            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": dict(bench_config(w, world), parallelism=f"sortfirst{world}"),
+            "frames_per_s": 1000.0 / ms, "samples_per_frame": samples,
+            "bands": part.per_rank, "gpu_launches": 8 * K, "clocks": clk.summary(),
+            "e2e": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    R.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
 
     from paper_1609_01317_gb300 import Renderer, build, vr
 
+    if args.mode == "sortfirst":
+        return run_sortfirst(args)
     rank, world, local = dist_setup(args)
     build.build()
     w = workload(args.workload)
@@ -863,6 +1011,25 @@ def run_ours(args):
                      "peak_source": "vr_measure_peaks, best of 5: FP32 FMA chains; gather + "
                                     "blend of 8 corner records per sample, the better of "
                                     "random cells in L1 and the march's pattern in L2"}
+    # the method's own footprint: every visited sample gathers the 8 voxels of its cell in the
+    # volume's storage type (here at the better of the two measured 16-bit gather rates) ->
+    # T_roof = max(compulsory HBM, FP32 work at the FMA rate, those gathers); beside it the
+    # full neighbourhood footprint of the shaded samples (4^3 voxels for the 3x3x3 operators,
+    # the 32-voxel cross for central differences, counted as 8-voxel gathers), which the
+    # precomputed operator records avoid paying per sample
+    g_u16 = max(mp["gather_u16_random_gsps"], mp["gather_u16_coherent_gsps"])
+    hood = {"central": 32, "sobel3d": 64, "zucker_hummel": 64}[w["grad"]]
+    terms_vox = {"alu": terms["alu"], "hbm": terms["hbm"],
+                 "gather": stats["samples_visited"] / (g_u16 * 1e9) * 1e3}
+    bind_vox = max(terms_vox, key=terms_vox.get)
+    roof_voxel = {"bound": bind_vox, "t_roof_ms": terms_vox[bind_vox], "launch_ms": march_avg,
+                  "frac": terms_vox[bind_vox] / march_avg, "terms_ms": terms_vox,
+                  "gather_peak_gsps": g_u16,
+                  "neighbourhood_gather_ms": (stats["samples_visited"] + stats["samples_shaded"] * hood / 8)
+                  / (g_u16 * 1e9) * 1e3,
+                  "peak_source": "vr_measure_peaks, best of 5: 8 voxels of a cell in 16-bit "
+                                 "storage + trilinear blend, the better of random cells in L1 "
+                                 "and the march's pattern in L2"}
 
     line = {
         "metric": "Gsamples/s", "value": value, "unit": "Gsamples/s", "n_gpus": world,
@@ -884,6 +1051,7 @@ def run_ours(args):
         "roofline": roof,
         "roofline_hbm": roof_hbm,
         "roofline_measured": roof_measured,
+        "roofline_voxel_gather": roof_voxel,
         # per step: k_pad, k_brick_minmax, k_brick_visibility (upload); k_tf_prefix,
         # k_brick_visibility (transfer function); k_records, k_march (render)
         "gpu_launches": 7 * K,
@@ -894,6 +1062,7 @@ def run_ours(args):
     f16_img = f16_vol = None
     if not args.no_extras:
         line["f16"], f16_img, f16_vol = f16_leg(args, max(10, min(K, 50)))
+        line["sparse"] = sparse_leg(args, max(10, min(K, 50)))
         line["train"] = train_leg(R, args)
         line["fwd_bwd"] = fwd_bwd_leg(R, args)
         line["surface"] = surface_leg(R, args)
@@ -995,11 +1164,11 @@ def run_ours(args):
                           "pixels": int(err.size), "max_abs": float(err.max()),
                           "frac_within_2e-3": float((err <= 2e-3).mean()),
                           "mean_abs": float(np.abs(gpu - ref).mean())}
+        import oracle
+
         if f16_img is not None:
             # the FP16 frame against the FP64 oracle's frame of the same FP16 volume, whole
             # image (both storage variants' errors side by side)
-            import oracle
-
             t0 = time.perf_counter()
             ref16, _, _ = oracle.render(oracle.OracleVolume(f16_vol, 1.0), w["tf"], cam,
                                         oracle.make_params(step=w["step"], grad=w["grad"]))
@@ -1009,6 +1178,19 @@ def run_ours(args):
                                      "frac_within_2e-3": float((e16 <= 2e-3).mean()),
                                      "mean_abs": float(np.abs(f16_img - ref16).mean()),
                                      "oracle_s": time.perf_counter() - t0}
+        sp = line.get("sparse", {}).pop("_samples", None)
+        if sp is not None:
+            ws = sp["w"]
+            ref, _, _ = oracle.render_pixels(
+                oracle.OracleVolume(ws["volume"], ws["value_max"]), ws["tf"], ws["camera"],
+                oracle.make_params(step=ws["step"], grad=ws["grad"]), sp["pick"][:, 1],
+                sp["pick"][:, 0])
+            es = np.abs(sp["got"].astype(np.float64) - ref).max(axis=-1)
+            line["sparse"]["parity"] = {"reference": "FP64 oracle", "pixels": int(es.size),
+                                        "sample": "1500 pixels whose ray reaches something "
+                                                  "+ 300 anywhere",
+                                        "max_abs": float(es.max()),
+                                        "frac_within_2e-3": float((es <= 2e-3).mean())}
         bs = line.get("batch", {}).pop("_samples", None)
         if bs is not None:
             line["batch"]["parity"] = batch_parity(bs)
@@ -1021,8 +1203,9 @@ def run_ours(args):
     else:
         line["e2e"] = None
         line["cpu_baseline"] = None
-    if isinstance(line.get("batch"), dict):
-        line["batch"].pop("_samples", None)  # host copies kept only for the oracle comparison
+    for leg in ("batch", "sparse"):  # host copies kept only for the oracle comparison
+        if isinstance(line.get(leg), dict):
+            line[leg].pop("_samples", None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     R.close()
@@ -1047,6 +1230,9 @@ def run_leg(args):
         R.close()
     elif args.leg == "f16":
         out = f16_leg(args, max(10, min(args.steps, 50)))[0]
+    elif args.leg == "sparse":
+        out = sparse_leg(args, max(10, min(args.steps, 50)))
+        out.pop("_samples", None)
     else:
         out = batch_leg(args)
         out.pop("_samples", None)

@@ -21,7 +21,10 @@
  *     on it and is asynchronous unless the call says it synchronises.
  *   - Caller buffers are never freed or retained past the call; buffers the library needs
  *     (padded volume, brick tables, transfer function, staging, adjoint scratch) come from
- *     the allocator given to vr_create and are released by vr_destroy.
+ *     the allocator given to vr_create and are released by vr_destroy.  Besides, each
+ *     context holds 8 bytes of mapped pinned host memory (cudaHostAlloc) into which the GPU
+ *     writes the visible-brick count of each finished visibility refresh; renders read it
+ *     to choose between two marches that give the same pixels.
  *   - Volumes are dense x-fastest arrays: voxel (x, y, z) is element x + nx*(y + ny*z)
  *     and sits at world point (x, y, z) (unit spacing, §2.1 Eq. 1).
  *   - Alignment: a voxel array must be aligned to its element size; device images, image
@@ -169,6 +172,16 @@ vr_status vr_set_camera(vr_ctx *ctx, const vr_camera *cam);
  * rectangle (vr_screen_rect), and the pixels outside it, whose rays miss the box, are
  * cleared to (0, 0, 0, 0) first. */
 vr_status vr_render(vr_ctx *ctx, const vr_render_params *params, float *out_rgba, void *stream);
+
+/* Rows [row0, row1) of the image vr_render would produce for the current volume, transfer
+ * function and camera, written to out_rgba as a band of (row1 - row0) x W x 4 float32 (host
+ * or device memory, detected), bit for bit equal to those rows of vr_render's image.
+ * Rays are independent (§2.2, §6), so a frame can be split by rows over several GPUs that
+ * hold the same volume (the image-space, sort-first partition): each renders its bands and
+ * the bands are gathered.  With collect_stats = 1 the counters cover the band's rays.
+ * Errors: as vr_render, plus INVALID_ARG unless 0 <= row0 < row1 <= H. */
+vr_status vr_render_rows(vr_ctx *ctx, const vr_render_params *params, int row0, int row1,
+                         float *out_rgba, void *stream);
 
 /* Bytes of the checkpoint buffer vr_render_forward_train needs for the current camera,
  * volume and `params` (per-ray end index plus transmittance every 32 samples). */
@@ -359,10 +372,14 @@ typedef struct {
                                      quads of lanes on consecutive samples (step 0.5) of 4 x 2
                                      neighbouring rays 1.09 voxels apart, table in L2      */
     double gather_random_gsps;    /* the same at uniformly random cells of a 64 KiB table    */
+    double gather_u16_random_gsps;   /* the method's own per-sample footprint: the 8 voxels of
+                                        the sample's cell in 16-bit storage and their trilinear
+                                        blend, Gsamples/s, random cells of a 64 KiB volume      */
+    double gather_u16_coherent_gsps; /* the same in the march's pattern over a 32 MiB volume  */
 } vr_peaks;
 
-/* Time the three microbenchmarks of vr_peaks on `device` (synchronous; private stream and
- * buffers from cudaMalloc, about 33 MiB, released before returning), best of `repeats`
+/* Time the five microbenchmarks of vr_peaks on `device` (synchronous; private stream and
+ * buffers from cudaMalloc, about 65 MiB, released before returning), best of `repeats`
  * timed launches after one warm-up.  Errors: INVALID_ARG (out NULL, repeats outside
  * 1..1000, device < 0), OUT_OF_MEMORY, CUDA (no such device, a launch failed). */
 vr_status vr_measure_peaks(int device, int repeats, vr_peaks *out);

@@ -142,6 +142,18 @@ class Renderer:
         vr.vr_render(self.ctx, p, out, _stream_handle())
         return out
 
+    def render_rows(self, row0: int, row1: int, params=None, out=None, **kw):
+        """Rows [row0, row1) of ``render``'s image as a (row1 - row0, W, 4) float32 CUDA
+        tensor (bit for bit those rows of the whole frame)."""
+        torch = _torch()
+        p = params if params is not None else vr.make_params(**kw)
+        W = self.camera["width"]
+        if out is None:
+            out = torch.empty((row1 - row0, W, 4), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        vr.vr_render_rows(self.ctx, p, row0, row1, out, _stream_handle())
+        return out
+
     def render_surface(self, params=None, out=None, depth=None, **kw):
         """First-hit surface render of the current volume and camera (§3.11, §5.1); returns
         ((H, W, 4) float32 image, (H, W) float32 hit distances, +inf where nothing is hit)."""

@@ -105,6 +105,8 @@ VolDev vol_dev(const vr_ctx* ctx) {
   V.vis = ctx->brick_vis;
   V.mvis = ctx->macro_vis;
   for (int a = 0; a < 3; ++a) V.nm[a] = ctx->nm[a];
+  V.svis = ctx->super_vis;
+  for (int a = 0; a < 3; ++a) V.ns[a] = ctx->ns[a];
   V.bounds = ctx->stats + 7;
   return V;
 }
@@ -213,10 +215,39 @@ vr_status check_params(const vr_render_params* p) {
 
 static vr_status refresh_visibility(vr_ctx* ctx, cudaStream_t s) {
   if (!ctx->has_volume || !ctx->has_tf) return VR_OK;
+  if (!ctx->vis_hint) {
+    // pinned host memory the visibility kernel writes its count into (mapped, so no copy
+    // joins the stream); {-1, 0} until a refresh has finished
+    void* h = nullptr;
+    void* d = nullptr;
+    vr_status st = cuda_status(cudaHostAlloc(&h, 2 * sizeof(int), cudaHostAllocMapped));
+    if (st != VR_OK) return st;
+    st = cuda_status(cudaHostGetDevicePointer(&d, h, 0));
+    if (st != VR_OK) {
+      cudaFreeHost(h);
+      return st;
+    }
+    static_cast<int*>(h)[0] = -1;
+    static_cast<int*>(h)[1] = 0;
+    ctx->vis_hint = static_cast<volatile int*>(h);
+    ctx->vis_hint_dev = static_cast<int*>(d);
+  }
   const float scale = (float)(ctx->ntf - 1) / ctx->value_max;
   return cuda_status(
       launch_brick_visibility(ctx->brick_minmax, ctx->nb, ctx->tf_prefix, ctx->ntf, scale,
-                              ctx->brick_vis, ctx->brick_list, ctx->macro_vis, ctx->nm, s));
+                              ctx->brick_vis, ctx->brick_list, ctx->macro_vis, ctx->nm, s,
+                              ctx->super_vis, ctx->ns, ctx->vis_hint_dev));
+}
+
+// Which march a plain render launches: from the visible-brick count of the latest
+// visibility refresh the GPU has finished (1: tiles, 2: list; a count of an earlier transfer
+// function only costs speed, the image is the same either way), or 0 (decided on the device
+// from the current count) while none has arrived for a volume of this brick grid.
+static int march_mode_hint(vr_ctx* ctx) {
+  if (!ctx->vis_hint) return 0;
+  const int count = ctx->vis_hint[0], nbricks = ctx->vis_hint[1];
+  if (count < 0 || nbricks != ctx->nb[0] * ctx->nb[1] * ctx->nb[2]) return 0;
+  return (long long)count * kListDenom < nbricks ? 2 : 1;
 }
 
 // Operator gradient records for the current volume, operator and (with skipping) the
@@ -308,9 +339,11 @@ void screen_rect(const CamDev& c, const float lo[3], const float hi[3], int rect
   if (rect[2] <= rect[0] || rect[3] <= rect[1]) rect[0] = rect[1] = rect[2] = rect[3] = 0;
 }
 
+// Renders rows [row0, row1) of the image (row1 < 0: to the last row) into `out`, a band of
+// (row1 - row0) rows.
 static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* out,
                                int* ck_kend, float* ck_T, int nslots, cudaStream_t s,
-                               float* ck_Tend = nullptr) {
+                               float* ck_Tend = nullptr, int row0 = 0, int row1 = -1) {
   vr_status rst = ensure_records(ctx, p, s);
   if (rst != VR_OK) return rst;
   MarchLaunch L;
@@ -328,18 +361,37 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
   L.ck_T = ck_T;
   L.ck_Tend = ck_Tend;
   L.nslots = nslots;
-  L.rect[0] = L.rect[1] = 0;
+  L.row0 = row0;
+  L.row1 = row1 < 0 ? L.cam.height : row1;
+  L.rect[0] = 0;
+  L.rect[1] = L.row0;
   L.rect[2] = L.cam.width;
-  L.rect[3] = L.cam.height;
+  L.rect[3] = L.row1;
   if (!ck_kend) {
-    // march only the tiles of the box's screen rectangle; the other pixels are zero
-    // (checkpointed renders write every ray's checkpoints, so they march every tile)
+    // march only the tiles of the box's screen rectangle (within the band); the other
+    // pixels are zero (checkpointed renders write every ray's checkpoints, so they march
+    // every tile)
     screen_rect(L.cam, L.r.lo, L.r.hi, L.rect);
-    if (L.rect[0] > 0 || L.rect[1] > 0 || L.rect[2] < L.cam.width || L.rect[3] < L.cam.height) {
+    L.rect[1] = std::max(L.rect[1], L.row0);
+    L.rect[3] = std::min(L.rect[3], L.row1);
+    if (L.rect[3] <= L.rect[1] || L.rect[2] <= L.rect[0])
+      L.rect[0] = L.rect[1] = L.rect[2] = L.rect[3] = 0;
+    if (L.rect[0] > 0 || L.rect[1] > L.row0 || L.rect[2] < L.cam.width || L.rect[3] < L.row1) {
       vr_status st = cuda_status(cudaMemsetAsync(
-          out, 0, (size_t)L.cam.width * L.cam.height * sizeof(float4), s));
+          out, 0, (size_t)L.cam.width * (L.row1 - L.row0) * sizeof(float4), s));
       if (st != VR_OK) return st;
     }
+  }
+  if (!ck_kend && !p->adaptive && L.rect[2] > L.rect[0]) {
+    // plain render: the rays of the rectangle's tiles are set up and listed first
+    const size_t tiles = (size_t)((L.rect[2] + 3) / 4 - L.rect[0] / 4) *
+                         (size_t)((L.rect[3] + 1) / 2 - L.rect[1] / 2);
+    vr_status st = ensure(ctx, &ctx->ray_list, &ctx->ray_list_cap, 256 + tiles * 8 * sizeof(RayRec));
+    if (st != VR_OK) return st;
+    L.list_head = static_cast<int*>(ctx->ray_list);
+    L.list = reinterpret_cast<RayRec*>(static_cast<char*>(ctx->ray_list) + 256);
+    L.vis_count = ctx->brick_list;  // [0]: visible bricks
+    L.mode = (p->skip_empty && L.V.mvis) ? march_mode_hint(ctx) : 1;
   }
   if (p->collect_stats) {
     vr_status st = cuda_status(cudaMemsetAsync(ctx->stats, 0, 4 * sizeof(unsigned long long), s));
@@ -441,6 +493,7 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->brick_minmax);
   ctx_free(ctx, ctx->upload_staging);
   if (ctx->host_copy_done) cudaEventDestroy(ctx->host_copy_done);
+  if (ctx->vis_hint) cudaFreeHost(const_cast<int*>(ctx->vis_hint));
   ctx_free(ctx, ctx->tf);
   ctx_free(ctx, ctx->stats);
   ctx_free(ctx, ctx->out_staging);
@@ -450,6 +503,7 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->surf_vis);
   ctx_free(ctx, ctx->adapt_mult);
   ctx_free(ctx, ctx->rec);
+  ctx_free(ctx, ctx->ray_list);
   delete ctx;
 }
 
@@ -506,25 +560,32 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
   const int nm[3] = {(nb[0] + 3) >> kMacroShift, (nb[1] + 3) >> kMacroShift,
                      (nb[2] + 3) >> kMacroShift};
   const size_t nmacro = (size_t)nm[0] * nm[1] * nm[2];
+  const int ns[3] = {(nm[0] + 3) >> kSuperShift, (nm[1] + 3) >> kSuperShift,
+                     (nm[2] + 3) >> kSuperShift};
+  const size_t nsuper = (size_t)ns[0] * ns[1] * ns[2];
   const size_t off_vis = align256(nbricks * sizeof(float2));
   const size_t off_list = off_vis + align256(nbricks);
   const size_t off_macro = off_list + align256((nbricks + 1) * sizeof(int));
-  st = ensure(ctx, &bt, &ctx->brick_cap, off_macro + nmacro);
+  const size_t off_super = off_macro + align256(nmacro);
+  // after the super flags: the block counter of the visibility kernel's count hint
+  st = ensure(ctx, &bt, &ctx->brick_cap, off_super + ((nsuper + 3) & ~(size_t)3) + sizeof(unsigned));
   ctx->brick_minmax = static_cast<float2*>(bt);
   if (st != VR_OK) {
-    ctx->brick_vis = ctx->macro_vis = nullptr;
+    ctx->brick_vis = ctx->macro_vis = ctx->super_vis = nullptr;
     ctx->brick_list = nullptr;
     return st;
   }
   ctx->brick_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) + off_vis);
   ctx->brick_list = reinterpret_cast<int*>(static_cast<char*>(bt) + off_list);
   ctx->macro_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) + off_macro);
+  ctx->super_vis = reinterpret_cast<uint8_t*>(static_cast<char*>(bt) + off_super);
   ctx->dtype = dtype;
   ctx->n[0] = nx; ctx->n[1] = ny; ctx->n[2] = nz;
   ctx->px = (int)px; ctx->py = (int)py; ctx->pz = (int)pz;
   for (int a = 0; a < 3; ++a) {
     ctx->nb[a] = nb[a];
     ctx->nm[a] = nm[a];
+    ctx->ns[a] = ns[a];
   }
   ctx->value_max = value_max;
   st = cuda_status(launch_pad_volume(src, (int)dtype, ctx->n, ctx->vol, ctx->px, ctx->py,
@@ -537,6 +598,8 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
     st = cuda_status(cudaMemsetAsync(ctx->brick_vis, 1, nbricks, s));
     if (st != VR_OK) return st;
     st = cuda_status(cudaMemsetAsync(ctx->macro_vis, 1, nmacro, s));
+    if (st != VR_OK) return st;
+    st = cuda_status(cudaMemsetAsync(ctx->super_vis, 1, nsuper, s));
     if (st != VR_OK) return st;
   }
   ctx->has_volume = true;
@@ -617,6 +680,33 @@ vr_status vr_render(vr_ctx* ctx, const vr_render_params* params, float* out_rgba
     dst = static_cast<float*>(ctx->out_staging);
   }
   st = render_common(ctx, params, dst, nullptr, nullptr, 0, s);
+  if (st != VR_OK) return st;
+  if (host_out)
+    st = cuda_status(cudaMemcpyAsync(out_rgba, dst, bytes, cudaMemcpyDeviceToHost, s));
+  return st;
+}
+
+vr_status vr_render_rows(vr_ctx* ctx, const vr_render_params* params, int row0, int row1,
+                         float* out_rgba, void* stream) {
+  TraceRange trace_("vr_render_rows");
+  if (!ctx || !out_rgba) return VR_ERR_INVALID_ARG;
+  vr_status st = check_params(params);
+  if (st != VR_OK) return st;
+  if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
+  if (row0 < 0 || row1 <= row0 || row1 > ctx->cam.height) return VR_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->cam.width * (row1 - row0) * sizeof(float4);
+  float* dst = out_rgba;
+  const bool host_out = !is_device_pointer(out_rgba);
+  if (!host_out && !aligned_to(out_rgba, 16)) return VR_ERR_INVALID_ARG;
+  if (host_out) {
+    st = ensure(ctx, &ctx->out_staging, &ctx->out_cap, bytes);
+    if (st != VR_OK) return st;
+    dst = static_cast<float*>(ctx->out_staging);
+  }
+  st = render_common(ctx, params, dst, nullptr, nullptr, 0, s, nullptr, row0, row1);
   if (st != VR_OK) return st;
   if (host_out)
     st = cuda_status(cudaMemcpyAsync(out_rgba, dst, bytes, cudaMemcpyDeviceToHost, s));

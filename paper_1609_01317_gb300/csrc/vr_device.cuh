@@ -15,6 +15,7 @@ namespace vr {
 constexpr int kBrick = 8;       // brick edge in voxels (empty-space skipping, §5.3)
 constexpr int kBrickShift = 3;
 constexpr int kMacroShift = 2;  // a macro brick is 4 x 4 x 4 bricks (32^3 voxels)
+constexpr int kSuperShift = 2;  // a super brick is 4 x 4 x 4 macro bricks (128^3 voxels)
 constexpr int kCkptStride = 32; // samples per adjoint checkpoint segment
 constexpr int kPadLo = 1;       // clamp-to-edge border below each axis
 constexpr int kPadHi = 2;       // ... and above (covers the 4^3 stencil of the last cell)
@@ -41,6 +42,8 @@ struct VolDev {
   const uint8_t* vis;  // per-brick visibility (1 = some sample may be non-transparent)
   const uint8_t* mvis;  // per-macro-brick visibility (OR over its bricks), or null
   int nm[3];            // macro bricks per axis
+  const uint8_t* svis = nullptr;  // per-super-brick visibility (OR over its macro bricks), or
+  int ns[3] = {0, 0, 0};          // null; super bricks per axis
   unsigned long long* bounds = nullptr;  // out-of-range index counter (bounds-checked builds)
 };
 

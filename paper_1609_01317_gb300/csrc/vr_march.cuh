@@ -65,20 +65,21 @@ __device__ __forceinline__ void corners_gradient(const Corners& k, const Cell& c
 // the macro index is monotone along the ray) takes samples k, k + m, k + 2m, k + 3m; any
 // other group takes the next 1-4 consecutive samples up to a multiple of 4 (so the following
 // group starts aligned to every multiplier) and drops the samples off their region's grid.
+// march_core: the march of a ray whose set-up (o, d, tn, K) is given, from sample k0 (a
+// multiple of 4; every sample before it lies in a transparent macro brick, so it contributes
+// nothing).
 template <bool CKPT, bool TFS = false, bool ADAPT = false>
-__device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, bool active,
-                                          int q, unsigned qmask, unsigned& hit, unsigned& plain,
-                                          unsigned& visited, unsigned& shaded,
-                                          const float4* s_tf = nullptr) {
+__device__ __forceinline__ void march_core(const MarchLaunch& L, const float o[3],
+                                           const float d[3], float tn, int K, int k0, int px,
+                                           int py, bool active, int q, unsigned qmask,
+                                           unsigned& hit, unsigned& plain, unsigned& visited,
+                                           unsigned& shaded, const float4* s_tf) {
   static_assert(!(CKPT && ADAPT), "the adjoint's checkpoints follow the regular grid");
   const int W = L.cam.width, H = L.cam.height;
   const int ray = py * W + px;
   const int qbase = (threadIdx.x & 31) & ~3;
-  float o[3], d[3], tn = 0.0f;
-  int K = 0;
-  if (active) ray_setup(L.cam, L.r.lo, L.r.hi, L.r.step, px, py, o, d, tn, K);
   float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
-  int k = 0;
+  int k = k0;
   const float step = L.r.step;
   const float inv_step = 1.0f / step;
   float inv_d[3];
@@ -142,6 +143,16 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
             b[1] = m[1];
             b[2] = m[2];
             shift = kBrickShift + kMacroShift;
+            if (L.V.svis) {
+              const int u[3] = {m[0] >> kSuperShift, m[1] >> kSuperShift, m[2] >> kSuperShift};
+              if (!__ldg(L.V.svis + VR_CHECK(L.V.bounds, u[0] + L.V.ns[0] * (u[1] + L.V.ns[1] * u[2]),
+                                             0, L.V.ns[0] * L.V.ns[1] * L.V.ns[2] - 1))) {
+                b[0] = u[0];
+                b[1] = u[1];
+                b[2] = u[2];
+                shift = kBrickShift + kMacroShift + kSuperShift;
+              }
+            }
           }
         }
         kn = region_exit_sample(b, shift, o, d, inv_d, tn, inv_step);
@@ -265,7 +276,8 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
     C2 += __shfl_xor_sync(qmask, C2, 2);
   }
   if (active && q == 0) {
-    reinterpret_cast<float4*>(L.out)[ray] = make_float4(C0, C1, C2, 1.0f - T);
+    reinterpret_cast<float4*>(L.out)[(size_t)(py - L.row0) * W + px] =
+        make_float4(C0, C1, C2, 1.0f - T);
     if (CKPT) {
       L.ck_kend[ray] = kend;
       L.ck_Tend[ray] = T;
@@ -273,6 +285,19 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
     hit += K > 0 ? 1u : 0u;
     plain += (unsigned)kend;
   }
+}
+
+// The march of pixel (px, py): ray set-up (§3.3, §3.6), then march_core from sample 0.
+template <bool CKPT, bool TFS = false, bool ADAPT = false>
+__device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, bool active,
+                                          int q, unsigned qmask, unsigned& hit, unsigned& plain,
+                                          unsigned& visited, unsigned& shaded,
+                                          const float4* s_tf = nullptr) {
+  float o[3], d[3], tn = 0.0f;
+  int K = 0;
+  if (active) ray_setup(L.cam, L.r.lo, L.r.hi, L.r.step, px, py, o, d, tn, K);
+  march_core<CKPT, TFS, ADAPT>(L, o, d, tn, K, 0, px, py, active, q, qmask, hit, plain,
+                               visited, shaded, s_tf);
 }
 
 }  // namespace vr

@@ -68,6 +68,8 @@ _SIGS = [
     ("vr_set_transfer_function", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     ("vr_set_camera", C.c_int, [C.c_void_p, C.POINTER(vr_camera)]),
     ("vr_render", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p, C.c_void_p]),
+    ("vr_render_rows", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_int, C.c_int,
+                                 C.c_void_p, C.c_void_p]),
     ("vr_checkpoint_bytes", C.c_int, [C.c_void_p, C.POINTER(vr_render_params),
                                       C.POINTER(C.c_size_t)]),
     ("vr_render_forward_train", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p,
@@ -252,11 +254,22 @@ def vr_set_camera(ctx, cam):
     c = cam if isinstance(cam, vr_camera) else make_camera(cam)
     _check("vr_set_camera", lib().vr_set_camera(ctx, C.byref(c)))
     _state.setdefault(ctx, {})["image"] = _image_bytes(c)
+    _state[ctx]["height"] = int(c.height)
 
 
 def vr_render(ctx, params, out_rgba, stream=None):
     _buf("vr_render", out_rgba, _state.get(ctx, {}).get("image", 0), 4, what="out_rgba")
     _check("vr_render", lib().vr_render(ctx, C.byref(params), _ptr(out_rgba), stream))
+
+
+def vr_render_rows(ctx, params, row0, row1, out_rgba, stream=None):
+    """Rows [row0, row1) of vr_render's image into a (row1 - row0) x W x 4 band."""
+    img = _state.get(ctx, {}).get("image", 0)
+    H = _state.get(ctx, {}).get("height", 0)
+    band = img // H * (int(row1) - int(row0)) if H and row1 > row0 else 0
+    _buf("vr_render_rows", out_rgba, band, 4, what="out_rgba")
+    _check("vr_render_rows", lib().vr_render_rows(ctx, C.byref(params), int(row0), int(row1),
+                                                  _ptr(out_rgba), stream))
 
 
 def vr_checkpoint_bytes(ctx, params) -> int:
@@ -392,14 +405,14 @@ def vr_read_bounds_violations(ctx, stream=None) -> int:
 
 class vr_peaks(C.Structure):
     _fields_ = [("fma_tflops", C.c_double), ("gather_coherent_gsps", C.c_double),
-                ("gather_random_gsps", C.c_double)]
+                ("gather_random_gsps", C.c_double), ("gather_u16_random_gsps", C.c_double),
+                ("gather_u16_coherent_gsps", C.c_double)]
 
 
 def vr_measure_peaks(device=0, repeats=5) -> dict:
     p = vr_peaks()
     _check("vr_measure_peaks", lib().vr_measure_peaks(int(device), int(repeats), C.byref(p)))
-    return {"fma_tflops": p.fma_tflops, "gather_coherent_gsps": p.gather_coherent_gsps,
-            "gather_random_gsps": p.gather_random_gsps}
+    return {k: getattr(p, k) for k, _ in vr_peaks._fields_}
 
 
 def vr_status_string(status) -> str:

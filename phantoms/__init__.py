@@ -175,6 +175,68 @@ def ct_phantom(seed: int = 2, shape=(512, 512, 361), noise_sigma: float = 30.0) 
     return vol.astype(np.uint16)
 
 
+def vessels(seed: int = 5, shape=(512, 512, 512), tubes: int = 40, shells: int = 3,
+            noise_sigma: float = 30.0) -> np.ndarray:
+    """Sparse uint16 phantom (12-bit values): a tree of thin vessel-like tubes and thin
+    spherical shells in empty space (air exactly 0), for the hierarchical skipping of §5.4.
+
+    ``shape`` is (nx, ny, nz).  Every tube starts within 0.08 of the edge lengths of one
+    root point (drawn in the central fifth) and follows a smooth random walk (unit steps
+    whose direction turns by a small random amount, reflected at the volume faces) of
+    150-400 steps, with a radius tapering from U[2, 3.5] to 1 voxel and a value
+    U[2000, 3500]; each shell is 2 voxels thick with a radius U[0.04, 0.1] of the smallest
+    edge, centred within 0.2 of the edges of the root, value U[2500, 3500].  Gaussian noise
+    of sigma ``noise_sigma`` inside the structures only.  At the default size under 0.5 %
+    of the voxels are non-zero."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    n = np.array([nx, ny, nz], np.float64)
+    vol = np.zeros((nz, ny, nx), np.float64)
+
+    def ball(p, r, val):
+        (x0, x1), (y0, y1), (z0, z1) = _grid_box(vol.shape, p - r, p + r)
+        if x1 < x0 or y1 < y0 or z1 < z0:
+            return
+        z, y, x = np.meshgrid(np.arange(z0, z1 + 1), np.arange(y0, y1 + 1),
+                              np.arange(x0, x1 + 1), indexing="ij")
+        m = (x - p[0]) ** 2 + (y - p[1]) ** 2 + (z - p[2]) ** 2 <= r * r
+        sub = vol[z0:z1 + 1, y0:y1 + 1, x0:x1 + 1]
+        sub[m] = np.maximum(sub[m], val)
+
+    root = rng.uniform(0.4, 0.6, 3) * (n - 1.0)
+    for _ in range(tubes):
+        p = root + rng.uniform(-0.08, 0.08, 3) * n
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        steps = int(rng.integers(150, 401))
+        r0 = rng.uniform(2.0, 3.5)
+        val = rng.uniform(2000.0, 3500.0)
+        for i in range(steps):
+            ball(p, r0 + (1.0 - r0) * i / steps, val)
+            d = d + rng.normal(0.0, 0.12, 3)
+            d /= np.linalg.norm(d)
+            p = p + d
+            for a in range(3):  # reflect at the faces
+                if p[a] < 2.0 or p[a] > n[a] - 3.0:
+                    d[a] = -d[a]
+                    p[a] = min(max(p[a], 2.0), n[a] - 3.0)
+    for _ in range(shells):
+        c = root + rng.uniform(-0.2, 0.2, 3) * n
+        radius = rng.uniform(0.04, 0.1) * float(n.min())
+        val = rng.uniform(2500.0, 3500.0)
+        (x0, x1), (y0, y1), (z0, z1) = _grid_box(vol.shape, c - radius - 1, c + radius + 1)
+        z, y, x = np.meshgrid(np.arange(z0, z1 + 1), np.arange(y0, y1 + 1),
+                              np.arange(x0, x1 + 1), indexing="ij")
+        dist = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+        m = np.abs(dist - radius) <= 1.0
+        sub = vol[z0:z1 + 1, y0:y1 + 1, x0:x1 + 1]
+        sub[m] = np.maximum(sub[m], val)
+    inside = vol > 0
+    vol[inside] += rng.normal(0.0, noise_sigma, int(inside.sum()))
+    vol = np.clip(np.rint(vol), 0.0, U12_MAX)
+    return vol.astype(np.uint16)
+
+
 def density_phantom(seed: int = 3, n: int = 128, count: int = 5) -> np.ndarray:
     """Hidden float32 density phantom in [0, 1]: five overlapping ellipsoids."""
     rng = np.random.default_rng(seed)
@@ -360,6 +422,21 @@ def workload_ct(width=1920, height=1080, shape=(512, 512, 361), azimuth=0.6, ele
     cam = orbit_camera(shape, width, height, azimuth, elevation, 40.0)
     tf = tf_two_plateau(256, soft=(900.0, 1300.0))
     return {"name": f"ct{shape[0]}x{shape[1]}x{shape[2]}_u16_persp{width}x{height}_zh",
+            "volume": vol, "value_max": U12_MAX, "tf": tf, "camera": cam,
+            "grad": "zucker_hummel", "step": 0.5, "skip_empty": True}
+
+
+def workload_sparse(width=3840, height=2160, shape=(512, 512, 512), azimuth=2.3,
+                    elevation=0.45):
+    """512^3 uint16 sparse vessel phantom (seed 5), perspective 3840x2160 (fov 40, orbit
+    2x diagonal), Zucker-Hummel, step 0.5, skipping + termination; transfer function: the
+    tubes and shells (alpha 0.35 above raw 1800, reddish to white), air and noise floor
+    transparent."""
+    vol = vessels(5, shape)
+    cam = orbit_camera(shape, width, height, azimuth, elevation, 40.0)
+    tf = tf_two_plateau(256, soft=(1900.0, 2300.0), soft_alpha=0.35, bone=(2300.0, 4095.0),
+                        bone_alpha=0.5)
+    return {"name": f"vessels{shape[0]}x{shape[1]}x{shape[2]}_u16_persp{width}x{height}_zh",
             "volume": vol, "value_max": U12_MAX, "tf": tf, "camera": cam,
             "grad": "zucker_hummel", "step": 0.5, "skip_empty": True}
 

@@ -21,3 +21,6 @@ def test_measured_peaks_are_plausible():
     # a sample's gather moves 128 bytes through L1: far below 100 TB/s of gathered bytes
     for k in ("gather_coherent_gsps", "gather_random_gsps"):
         assert pk[k] * 128 < 100e3
+    # the 8 voxels of a cell in 16-bit storage are 16 bytes per sample
+    for k in ("gather_u16_random_gsps", "gather_u16_coherent_gsps"):
+        assert pk[k] * 16 < 100e3
