@@ -22,9 +22,9 @@
  *   - Caller buffers are never freed or retained past the call; buffers the library needs
  *     (padded volume, brick tables, transfer function, staging, adjoint scratch) come from
  *     the allocator given to vr_create and are released by vr_destroy.  Besides, each
- *     context holds 8 bytes of mapped pinned host memory (cudaHostAlloc) into which the GPU
- *     writes the visible-brick count of each finished visibility refresh; renders read it
- *     to choose between two marches that give the same pixels.
+ *     context holds 8 bytes of mapped pinned host memory (cudaHostAlloc) into which each
+ *     render's march writes the visible-brick count it saw; the next render reads it to
+ *     choose between two marches that give the same pixels.
  *   - Volumes are dense x-fastest arrays: voxel (x, y, z) is element x + nx*(y + ny*z)
  *     and sits at world point (x, y, z) (unit spacing, §2.1 Eq. 1).
  *   - Alignment: a voxel array must be aligned to its element size; device images, image

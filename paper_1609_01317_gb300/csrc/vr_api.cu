@@ -215,34 +215,37 @@ vr_status check_params(const vr_render_params* p) {
 
 static vr_status refresh_visibility(vr_ctx* ctx, cudaStream_t s) {
   if (!ctx->has_volume || !ctx->has_tf) return VR_OK;
-  if (!ctx->vis_hint) {
-    // pinned host memory the visibility kernel writes its count into (mapped, so no copy
-    // joins the stream); {-1, 0} until a refresh has finished
-    void* h = nullptr;
-    void* d = nullptr;
-    vr_status st = cuda_status(cudaHostAlloc(&h, 2 * sizeof(int), cudaHostAllocMapped));
-    if (st != VR_OK) return st;
-    st = cuda_status(cudaHostGetDevicePointer(&d, h, 0));
-    if (st != VR_OK) {
-      cudaFreeHost(h);
-      return st;
-    }
-    static_cast<int*>(h)[0] = -1;
-    static_cast<int*>(h)[1] = 0;
-    ctx->vis_hint = static_cast<volatile int*>(h);
-    ctx->vis_hint_dev = static_cast<int*>(d);
-  }
   const float scale = (float)(ctx->ntf - 1) / ctx->value_max;
   return cuda_status(
       launch_brick_visibility(ctx->brick_minmax, ctx->nb, ctx->tf_prefix, ctx->ntf, scale,
                               ctx->brick_vis, ctx->brick_list, ctx->macro_vis, ctx->nm, s,
-                              ctx->super_vis, ctx->ns, ctx->vis_hint_dev));
+                              ctx->super_vis, ctx->ns));
 }
 
-// Which march a plain render launches: from the visible-brick count of the latest
-// visibility refresh the GPU has finished (1: tiles, 2: list; a count of an earlier transfer
-// function only costs speed, the image is the same either way), or 0 (decided on the device
-// from the current count) while none has arrived for a volume of this brick grid.
+// Which march a plain render launches: from the visible-brick count the previous plain
+// render's march saw (1: tiles, 2: list; a count of an earlier transfer function only costs
+// speed, the image is the same either way), or 0 (decided on the device from the current
+// count) while none has arrived for a volume of this brick grid.
+static vr_status ensure_hint(vr_ctx* ctx) {
+  if (ctx->vis_hint) return VR_OK;
+  // mapped pinned host memory the march writes the count into (no copy joins the stream);
+  // {-1, 0} until a march has written it
+  void* h = nullptr;
+  void* d = nullptr;
+  vr_status st = cuda_status(cudaHostAlloc(&h, 2 * sizeof(int), cudaHostAllocMapped));
+  if (st != VR_OK) return st;
+  st = cuda_status(cudaHostGetDevicePointer(&d, h, 0));
+  if (st != VR_OK) {
+    cudaFreeHost(h);
+    return st;
+  }
+  static_cast<int*>(h)[0] = -1;
+  static_cast<int*>(h)[1] = 0;
+  ctx->vis_hint = static_cast<volatile int*>(h);
+  ctx->vis_hint_dev = static_cast<int*>(d);
+  return VR_OK;
+}
+
 static int march_mode_hint(vr_ctx* ctx) {
   if (!ctx->vis_hint) return 0;
   const int count = ctx->vis_hint[0], nbricks = ctx->vis_hint[1];
@@ -391,6 +394,9 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
     L.list_head = static_cast<int*>(ctx->ray_list);
     L.list = reinterpret_cast<RayRec*>(static_cast<char*>(ctx->ray_list) + 256);
     L.vis_count = ctx->brick_list;  // [0]: visible bricks
+    st = ensure_hint(ctx);
+    if (st != VR_OK) return st;
+    L.hint = ctx->vis_hint_dev;
     L.mode = (p->skip_empty && L.V.mvis) ? march_mode_hint(ctx) : 1;
   }
   if (p->collect_stats) {
@@ -567,8 +573,7 @@ vr_status vr_upload_volume(vr_ctx* ctx, const void* voxels, vr_dtype dtype, int 
   const size_t off_list = off_vis + align256(nbricks);
   const size_t off_macro = off_list + align256((nbricks + 1) * sizeof(int));
   const size_t off_super = off_macro + align256(nmacro);
-  // after the super flags: the block counter of the visibility kernel's count hint
-  st = ensure(ctx, &bt, &ctx->brick_cap, off_super + ((nsuper + 3) & ~(size_t)3) + sizeof(unsigned));
+  st = ensure(ctx, &bt, &ctx->brick_cap, off_super + nsuper);
   ctx->brick_minmax = static_cast<float2*>(bt);
   if (st != VR_OK) {
     ctx->brick_vis = ctx->macro_vis = ctx->super_vis = nullptr;

@@ -109,9 +109,9 @@ struct vr_ctx {
   // records from byte 256 on)
   void* ray_list = nullptr;
   size_t ray_list_cap = 0;
-  // the visible-brick count of the latest visibility refresh the GPU has finished, written
-  // by k_brick_visibility into mapped pinned host memory: {count, bricks} (a hint for
-  // choosing the march; read without waiting)
+  // the visible-brick count seen by the latest plain render's march, written by the march
+  // into mapped pinned host memory: {count, bricks} (a hint for choosing the next render's
+  // march; read without waiting)
   volatile int* vis_hint = nullptr;
   int* vis_hint_dev = nullptr;  // the same memory as the device sees it
 
@@ -164,14 +164,12 @@ cudaError_t launch_tf_prefix(const float4* tf, int n, int* prefix, cudaStream_t 
 // vis[b] for every brick; when `list` is non-null, its visible bricks' indices are written
 // after list[0] (= their count, order unspecified); when `mvis` is non-null, mvis[m] = OR of
 // vis over the bricks of macro brick m (grid nm), and when `svis` is non-null too, svis[u] =
-// OR over the macro bricks of super brick u (grid ns; the allocation holds 4 more bytes
-// after the ns[0] ns[1] ns[2] flags, rounded up to 4, for a block counter); when `hint` is
-// non-null too, the last block to finish writes {list[0], bricks} there (host-mapped memory)
+// OR over the macro bricks of super brick u (grid ns; svis must follow mvis in the same
+// allocation: both are cleared by one memset)
 cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
                                     int ntf, float scale, uint8_t* vis, int* list,
                                     uint8_t* mvis, const int nm[3], cudaStream_t s,
-                                    uint8_t* svis = nullptr, const int* ns = nullptr,
-                                    int* hint = nullptr);
+                                    uint8_t* svis = nullptr, const int* ns = nullptr);
 // mult[m] = 4 if the footprint range max - min of macro brick m is <= r4 (r4 >= 0), else 2
 // if <= r2 (r2 >= 0), else 1
 cudaError_t launch_macro_multiplier(const float2* mm, const int nb[3], const int nm[3], float r2,
@@ -223,6 +221,7 @@ struct MarchLaunch {
   int* list_head = nullptr;  // [0]: rays listed, [1]: the march's work counter (zeroed per launch)
   const int* vis_count = nullptr;  // visible bricks of the current transfer function (device)
   int mode = 0;  // 0: list mode decided on the device from vis_count; 1: tiles; 2: list
+  int* hint = nullptr;  // host-mapped {count, bricks}: written by the march for the next render
 };
 cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s);
 // Pixel rectangle [rect[0], rect[2]) x [rect[1], rect[3]) outside which every ray of camera c

@@ -39,6 +39,15 @@ __device__ __forceinline__ bool list_mode(const MarchLaunch& L) {
   return (long long)__ldg(L.vis_count) * kListDenom < nbricks;
 }
 
+// The first thread of the grid passes the visible-brick count on to the host for the next
+// render's choice of march (mapped pinned memory; a posted write under a long kernel).
+__device__ __forceinline__ void write_hint(const MarchLaunch& L) {
+  if (L.hint && L.vis_count && blockIdx.x == 0 && threadIdx.x == 0) {
+    L.hint[0] = __ldg(L.vis_count);
+    L.hint[1] = L.V.nb[0] * L.V.nb[1] * L.V.nb[2];
+  }
+}
+
 __device__ __forceinline__ void add_stats(const MarchLaunch& L, unsigned hit, unsigned plain,
                                           unsigned visited, unsigned shaded) {
   const int lane = threadIdx.x & 31;
@@ -60,6 +69,7 @@ __device__ __forceinline__ void add_stats(const MarchLaunch& L, unsigned hit, un
 template <bool CKPT, bool TFS, bool ADAPT = false>
 __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
   if constexpr (!CKPT && !ADAPT) {
+    write_hint(L);
     if (list_mode(L)) return;
   }
   extern __shared__ float4 s_tf[];
@@ -97,6 +107,7 @@ __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
 // keeps the tiles' order), a quad of lanes per ray, from each ray's first visible group.
 template <bool TFS>
 __global__ void __launch_bounds__(kThreads, 7) k_march_list(const MarchLaunch L) {
+  write_hint(L);
   if (!list_mode(L)) return;
   extern __shared__ float4 s_tf[];
   if constexpr (TFS) {

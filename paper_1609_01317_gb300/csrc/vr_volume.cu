@@ -214,8 +214,7 @@ __global__ void k_brick_visibility(const float2* __restrict__ mm, int nbx, int n
                                    const int* __restrict__ prefix, int ntf, float scale,
                                    uint8_t* __restrict__ vis, int* __restrict__ list,
                                    uint8_t* __restrict__ mvis, int nmx, int nmy,
-                                   uint8_t* __restrict__ svis, int nsx, int nsy,
-                                   unsigned* __restrict__ done, int* __restrict__ hint) {
+                                   uint8_t* __restrict__ svis, int nsx, int nsy) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool visible = false;
   if (i < nbricks) {
@@ -245,50 +244,30 @@ __global__ void k_brick_visibility(const float2* __restrict__ mm, int nbx, int n
     if (lane == 0 && m) base = atomicAdd(list, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (visible) list[1 + base + __popc(m & ((1u << lane) - 1u))] = i;
-    if (hint) {
-      // the last block to finish copies the final count out (every block's appends are
-      // complete and visible once its counter increment is)
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(done, 1u) == gridDim.x - 1) {
-          __threadfence();
-          hint[0] = *reinterpret_cast<volatile int*>(list);
-          hint[1] = nbricks;
-        }
-      }
-    }
   }
 }
 
 cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int* prefix,
                                     int ntf, float scale, uint8_t* vis, int* list,
                                     uint8_t* mvis, const int nm[3], cudaStream_t s,
-                                    uint8_t* svis, const int* ns, int* hint) {
+                                    uint8_t* svis, const int* ns) {
   const int nbricks = nb[0] * nb[1] * nb[2];
   const int threads = 256;
   if (list) {
     const cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
   }
-  if (mvis) {
-    const cudaError_t e = cudaMemsetAsync(mvis, 0, (size_t)nm[0] * nm[1] * nm[2], s);
-    if (e != cudaSuccess) return e;
-  }
   if (!mvis) svis = nullptr;
-  if (!svis || !list) hint = nullptr;
-  unsigned* done = nullptr;
-  if (svis) {
-    // the super flags and, after them, the block counter of the hint start at zero
-    const size_t nsuper = (size_t)ns[0] * ns[1] * ns[2];
-    const size_t off = (nsuper + 3) & ~(size_t)3;
-    done = reinterpret_cast<unsigned*>(svis + off);
-    const cudaError_t e = cudaMemsetAsync(svis, 0, off + sizeof(unsigned), s);
+  if (mvis) {
+    // the macro flags, and the super flags that follow them in the same allocation
+    const size_t bytes = svis ? (size_t)(svis - mvis) + (size_t)ns[0] * ns[1] * ns[2]
+                              : (size_t)nm[0] * nm[1] * nm[2];
+    const cudaError_t e = cudaMemsetAsync(mvis, 0, bytes, s);
     if (e != cudaSuccess) return e;
   }
   k_brick_visibility<<<(nbricks + threads - 1) / threads, threads, 0, s>>>(
       mm, nb[0], nb[1], nbricks, prefix, ntf, scale, vis, list, mvis, mvis ? nm[0] : 0,
-      mvis ? nm[1] : 0, svis, svis ? ns[0] : 0, svis ? ns[1] : 0, done, hint);
+      mvis ? nm[1] : 0, svis, svis ? ns[0] : 0, svis ? ns[1] : 0);
   return cudaGetLastError();
 }
 
