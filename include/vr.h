@@ -291,7 +291,10 @@ vr_status vr_render_backward_views(vr_ctx *ctx, const vr_render_params *params, 
                                    float *grad_tf, void *stream);
 
 /* Copy the counters of the last render with collect_stats = 1 into *out.  Synchronises
- * `stream`.  Errors: INVALID_ARG, STATE (no such render), CUDA. */
+ * `stream`.  Errors: INVALID_ARG, STATE (no such render), CUDA, TIMEOUT (an earlier pass that
+ * computes the operator gradient records gave up waiting, after about a second, for a copy
+ * of a brick's neighbourhood into shared memory: the records, and so images since, are
+ * incomplete; upload the volume again). */
 vr_status vr_read_stats(vr_ctx *ctx, vr_stats *out, void *stream);
 
 /* ---- Batched rendering -------------------------------------------------------------

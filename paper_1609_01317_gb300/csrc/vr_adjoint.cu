@@ -123,8 +123,12 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
   const unsigned qmask = 0xFu << (lane & ~3);
   const int W = L.cam.width, H = L.cam.height;
   const int nrays = W * H;
-  const int tiles_x = (W + kQuadTileW - 1) / kQuadTileW;
-  const int tiles = tiles_x * ((H + kQuadTileH - 1) / kQuadTileH);
+  // tiles covering the rectangle L.rect (the rays outside it miss the box: nothing to do)
+  const int rx1 = min(L.rect[2], W), ry1 = min(L.rect[3], H);
+  const int tx0 = L.rect[0] / kQuadTileW, ty0 = L.rect[1] / kQuadTileH;
+  const int tiles_x = (rx1 + kQuadTileW - 1) / kQuadTileW - tx0;
+  const int tiles = rx1 > L.rect[0] && ry1 > L.rect[1]
+                        ? tiles_x * ((ry1 + kQuadTileH - 1) / kQuadTileH - ty0) : 0;
   const float step = L.r.step;
   const float gs = L.r.gscale;
   for (;;) {
@@ -132,8 +136,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
     if (lane == 0) tile = (int)atomicAdd(L.tile_counter, 1u);
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= tiles) break;
-    const int px = (tile % tiles_x) * kQuadTileW + (qd & 3);
-    const int py = (tile / tiles_x) * kQuadTileH + (qd >> 2);
+    const int px = (tx0 + tile % tiles_x) * kQuadTileW + (qd & 3);
+    const int py = (ty0 + tile / tiles_x) * kQuadTileH + (qd >> 2);
     const bool active = px < W && py < H;
     const int ray = py * W + px;
     float o[3], d[3], tn = 0.0f;

@@ -270,7 +270,8 @@ vr_status ensure_records(vr_ctx* ctx, const vr_render_params* p, cudaStream_t s)
   }
   st = cuda_status(launch_records(vol_dev(ctx), (int)ctx->dtype, p->grad,
                                   skip ? ctx->brick_vis : nullptr,
-                                  skip ? ctx->brick_list : nullptr, ctx->rec, s));
+                                  skip ? ctx->brick_list : nullptr, ctx->rec, s,
+                                  reinterpret_cast<unsigned*>(ctx->stats + 8)));
   if (st != VR_OK) {
     ctx->rec_valid = false;
     return st;
@@ -372,8 +373,9 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
   L.rect[3] = L.row1;
   if (!ck_kend) {
     // march only the tiles of the box's screen rectangle (within the band); the other
-    // pixels are zero (checkpointed renders write every ray's checkpoints, so they march
-    // every tile)
+    // pixels are zero.  A checkpointed render marches every tile: its rays outside the
+    // rectangle miss the box and record end index 0 without any memset (the adjoint skips
+    // the rectangle's outside)
     screen_rect(L.cam, L.r.lo, L.r.hi, L.rect);
     L.rect[1] = std::max(L.rect[1], L.row0);
     L.rect[3] = std::min(L.rect[3], L.row1);
@@ -473,14 +475,14 @@ vr_status vr_create(vr_ctx** out, int device, vr_alloc_fn alloc, vr_free_fn free
     return cuda_status(cudaGetLastError());
   }
   void* st = nullptr;
-  const vr_status s = ctx_alloc(ctx, &st, 8 * sizeof(unsigned long long));
+  const vr_status s = ctx_alloc(ctx, &st, 16 * sizeof(unsigned long long));
   if (s != VR_OK) {
     delete ctx;
     return s;
   }
   ctx->stats = static_cast<unsigned long long*>(st);
   // counters and work queues start at zero (the bounds counter is never reset)
-  const vr_status z = cuda_status(cudaMemset(ctx->stats, 0, 8 * sizeof(unsigned long long)));
+  const vr_status z = cuda_status(cudaMemset(ctx->stats, 0, 16 * sizeof(unsigned long long)));
   const vr_status zs = z == VR_OK ? cuda_status(cudaDeviceSynchronize()) : z;
   if (zs != VR_OK) {
     ctx_free(ctx, ctx->stats);
@@ -859,6 +861,7 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
     L.adj = grad_volume ? ctx->adj : nullptr;
     L.grad_tf = grad_tf;
     L.tf_partial = tf_partial ? ctx->tf_partial : nullptr;
+    screen_rect(basis, L.r.lo, L.r.hi, L.rect);  // rays outside it recorded end index 0
     st = cuda_status(launch_adjoint(L, s));
     if (st != VR_OK) return st;
   }
@@ -887,12 +890,13 @@ vr_status vr_read_stats(vr_ctx* ctx, vr_stats* out, void* stream) {
   if (!ctx->stats_valid) return VR_ERR_STATE;
   DeviceGuard g(ctx->device);
   if (!g.ok) return cuda_status(cudaGetLastError());
-  unsigned long long h[4];
+  unsigned long long h[9];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   vr_status st = cuda_status(cudaMemcpyAsync(h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
   if (st != VR_OK) return st;
   st = cuda_status(cudaStreamSynchronize(s));
   if (st != VR_OK) return st;
+  if (h[8] & 1u) return VR_ERR_TIMEOUT;  // a records pass gave up waiting for a staged copy
   out->rays_hit = h[0];
   out->samples_plain = h[1];
   out->samples_visited = h[2];

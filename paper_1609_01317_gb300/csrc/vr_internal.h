@@ -78,7 +78,8 @@ struct vr_ctx {
   vr::CamDev camdev{};
 
   // statistics: [0..3] counters, then the tile counters of the march [4], the adjoint [5]
-  // and the surface renderer [6]
+  // and the surface renderer [6], the bounds-violation counter [7] and the records pass's
+  // timeout word [8] (16 slots)
   unsigned long long* stats = nullptr;
   bool stats_valid = false;
 
@@ -175,9 +176,11 @@ cudaError_t launch_brick_visibility(const float2* mm, const int nb[3], const int
 cudaError_t launch_macro_multiplier(const float2* mm, const int nb[3], const int nm[3], float r2,
                                     float r4, uint8_t* mult, cudaStream_t s);
 // records of the bricks in `list` (as built by launch_brick_visibility, `need` its vis
-// array), or of every brick when `list` is null
+// array), or of every brick when `list` is null; with `err` (a device word) the bricks'
+// neighbourhoods are staged by TMA copies, and a copy that does not complete within about a
+// second sets *err |= 1 and ends the launch (the records are then incomplete)
 cudaError_t launch_records(const VolDev& V, int dtype, int op, const uint8_t* need,
-                           const int* list, float4* rec, cudaStream_t s);
+                           const int* list, float4* rec, cudaStream_t s, unsigned* err = nullptr);
 
 // A plain render takes the ray list when fewer than one brick in kListDenom is visible for
 // the current transfer function (the count k_brick_visibility leaves in the brick list).
@@ -247,6 +250,9 @@ struct AdjointLaunch {
   // vector reductions; grad_tf then receives them through launch_tf_partial_reduce instead
   // of from the kernel
   float* tf_partial;
+  // pixels [rect[0], rect[2]) x [rect[1], rect[3]) whose tiles the launch visits; every ray
+  // outside misses the sampling box (its recorded end index is 0)
+  int rect[4] = {0, 0, 1 << 30, 1 << 30};
 };
 // whether the TF gradient goes through per-block partial rows for a table of ntf entries,
 // and the persistent grid the adjoint launches

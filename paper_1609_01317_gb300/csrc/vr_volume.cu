@@ -1,5 +1,10 @@
 // vr_volume.cu -- volume upload kernels: clamp-to-edge padded copy, per-brick min/max
 // footprints and per-brick visibility for empty-space skipping (§5.3, §5.4).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "vr_internal.h"
 
 namespace vr {
@@ -582,36 +587,277 @@ __global__ void __launch_bounds__(64) k_records(const VolDev V, const uint8_t* _
   }
 }
 
+// ------------------------------------------------ records with TMA-staged neighbourhoods
+// The same records, with each brick's clamp-to-edge neighbourhood brought into shared memory
+// by the tensor memory accelerator: a 3-D tiled copy (cp.async.bulk.tensor) of the padded
+// volume's box [x0, x0 + BX) x [8by, 8by + 11) x [8bz, 8bz + 11) (padded coordinates; the
+// padded index of voxel 8b - 1 is 8b, so x0 = 8bx keeps the copy's start on a 16-byte
+// boundary for 2- and 4-byte voxels, and x0 = 16 (bx / 2) for 1-byte voxels, which then
+// copy 32 columns) completes on an mbarrier.  Two raw stages are in flight: the copy of the
+// brick after next is issued as soon as a stage has been converted into the float tile, so
+// the march of loads overlaps the computation.  Rows beyond the padded array read as zero;
+// they only feed records of voxels outside the volume, which are not written.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier for at most about a second of SM clock.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > 2000000000ll) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+template <int VTYPE>
+struct TmaBox {
+  using T = typename VoxelT<VTYPE>::T;
+  static constexpr int BX = sizeof(T) == 1 ? 32 : 16;  // columns per copied row
+  static constexpr int BYTES = 11 * 11 * BX * (int)sizeof(T);
+  static constexpr int STAGE = (BYTES + 127) / 128 * 128;
+};
+
+template <int VTYPE, int OP>
+__global__ void __launch_bounds__(64) k_records_tma(const VolDev V, const uint8_t* __restrict__ need,
+                                                    const int* __restrict__ list,
+                                                    float4* __restrict__ rec,
+                                                    const __grid_constant__ CUtensorMap tmap,
+                                                    unsigned* __restrict__ err) {
+  using T = typename VoxelT<VTYPE>::T;
+  using B = TmaBox<VTYPE>;
+  __shared__ __align__(128) unsigned char raw[2][B::STAGE];
+  __shared__ __align__(16) float tile[11][11][12];  // [z][y][x], x padded to 12
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int abort_all;
+  const int t = threadIdx.x;
+  const int nbx = V.nb[0], nby = V.nb[1];
+  const int nbricks = nbx * nby * V.nb[2];
+  const int nx = V.n[0], ny = V.n[1], nz = V.n[2];
+  int u = 0, w = 0, ncol = 0;  // first column, row, columns of this thread (0: idle)
+  if (t < 32) {
+    u = 2 * (t & 3);
+    w = t >> 2;
+    ncol = 2;
+  } else if (t < 36) {
+    u = 2 * (t - 32);
+    w = kBrick;
+    ncol = 2;
+  } else if (t < 45) {
+    u = kBrick;
+    w = t - 36;
+    ncol = 1;
+  }
+  const int nwork = list ? list[0] : nbricks;
+  const size_t zstride = (size_t)nx * ny;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_all = 0;
+  }
+  __syncthreads();
+  auto issue = [&](int item, int s) {  // thread 0: the copy of item's neighbourhood
+    const int b = list ? list[1 + item] : item;
+    const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+    const int x0 = sizeof(T) == 1 ? 16 * (bx >> 1) : 8 * bx;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[s], B::BYTES);
+    tma_load_3d(raw[s], &tmap, &bar[s], x0, 8 * by, 8 * bz);
+  };
+  const int first = blockIdx.x;
+  if (t == 0) {
+    if (first < nwork) issue(first, 0);
+    if (first + (int)gridDim.x < nwork) issue(first + gridDim.x, 1);
+  }
+  int it = 0;
+  for (int item = first; item < nwork; item += gridDim.x, ++it) {
+    const int s = it & 1;
+    if (t == 0 && !mbar_wait_bounded(&bar[s], (unsigned)(it >> 1) & 1u)) {
+      abort_all = 1;
+      atomicOr(err, 1u);
+      // the other stage's copy may be in flight: wait for it (bounded) before leaving
+      if (item + (int)gridDim.x < nwork) mbar_wait_bounded(&bar[s ^ 1], (unsigned)((it + 1) >> 1) & 1u);
+    }
+    __syncthreads();
+    if (abort_all) return;
+    const int bid = list ? list[1 + item] : item;
+    const int bx = bid % nbx, by = (bid / nbx) % nby, bz = bid / (nbx * nby);
+    const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
+    // raw stage -> float tile: rows t and t + 64 of the 121, columns x0 - 1 .. x0 + 10
+    {
+      const T* src = reinterpret_cast<const T*>(raw[s]);
+      const int xoff = sizeof(T) == 1 ? 8 * (bx & 1) : 0;
+      for (int r = t; r < 121; r += 64) {
+        const T* row = src + r * B::BX + xoff;
+        float e[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) e[i] = to_float<VTYPE>(row[i]);
+        float4* dst = reinterpret_cast<float4*>(&tile[r / 11][r % 11][0]);
+        dst[0] = make_float4(e[0], e[1], e[2], e[3]);
+        dst[1] = make_float4(e[4], e[5], e[6], e[7]);
+        dst[2] = make_float4(e[8], e[9], e[10], e[11]);
+      }
+    }
+    __syncthreads();
+    if (t == 0 && item + 2 * (int)gridDim.x < nwork) issue(item + 2 * gridDim.x, s);
+    const int x = x0 + u, y = y0 + w;
+    if (ncol && x < nx && y < ny) {
+      const int ox = u == kBrick, oy = w == kBrick;
+      bool wr_lo = true, wr_top = false;
+      if (need) {
+        if (ox | oy) wr_lo = !need[(bx + ox) + nbx * ((by + oy) + nby * bz)];
+        if (z0 + kBrick < nz) wr_top = !need[(bx + ox) + nbx * ((by + oy) + nby * (bz + 1))];
+      } else {
+        wr_lo = !(ox | oy);
+      }
+      const int qn = min(kBrick + 1, nz - z0);
+      const size_t obase = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z0);
+      const long long olast = (long long)nx * ny * nz - 1;
+      float4* out = rec + obase;
+      if (wr_lo || (wr_top && qn > kBrick)) {
+        if (ncol == 2) {
+          const bool two = x + 1 < nx;
+          PlaneSums A[3], Bs[3];
+          plane_sums2<OP>(tile[0], u, w, A[0], Bs[0]);
+          plane_sums2<OP>(tile[1], u, w, A[1], Bs[1]);
+#pragma unroll
+          for (int q = 0; q <= kBrick; ++q) {
+            if (q < qn) {
+              plane_sums2<OP>(tile[q + 2], u, w, A[(q + 2) % 3], Bs[(q + 2) % 3]);
+              if (q < kBrick ? wr_lo : wr_top) {
+                out[VR_CHECK(V.bounds, q * zstride, -(long long)obase, olast - (long long)obase)] =
+                    record_of<OP>(A[q % 3], A[(q + 1) % 3], A[(q + 2) % 3]);
+                if (two)
+                  out[VR_CHECK(V.bounds, q * zstride + 1, -(long long)obase, olast - (long long)obase)] =
+                      record_of<OP>(Bs[q % 3], Bs[(q + 1) % 3], Bs[(q + 2) % 3]);
+              }
+            }
+          }
+        } else {
+          PlaneSums ps[3];
+          ps[0] = plane_sums<OP>(tile[0], u, w);
+          ps[1] = plane_sums<OP>(tile[1], u, w);
+#pragma unroll
+          for (int q = 0; q <= kBrick; ++q) {
+            if (q < qn) {
+              ps[(q + 2) % 3] = plane_sums<OP>(tile[q + 2], u, w);
+              if (q < kBrick ? wr_lo : wr_top)
+                out[VR_CHECK(V.bounds, q * zstride, -(long long)obase, olast - (long long)obase)] =
+                    record_of<OP>(ps[q % 3], ps[(q + 1) % 3], ps[(q + 2) % 3]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // the tile is rewritten for the next brick
+  }
+}
+
+// cuTensorMapEncodeTiled from the driver the runtime uses (null when unavailable).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// The tensor map of the padded volume for the records' neighbourhood copies.
+template <int VTYPE>
+static bool records_tensor_map(const VolDev& V, CUtensorMap* map) {
+  using T = typename VoxelT<VTYPE>::T;
+  const auto encode = tensor_map_encoder();
+  if (!encode) return false;
+  const CUtensorMapDataType dt = sizeof(T) == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t dims[3] = {(cuuint64_t)V.px, (cuuint64_t)V.py,
+                              (cuuint64_t)(V.n[2] + kPadLo + kPadHi)};
+  const cuuint64_t strides[2] = {(cuuint64_t)V.px * sizeof(T), (cuuint64_t)V.pxy * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)TmaBox<VTYPE>::BX, 11, 11};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(map, dt, 3, const_cast<void*>(V.data), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int VTYPE, int OP>
 static void launch_records_k(const VolDev& V, const uint8_t* need, const int* list, float4* rec,
-                             cudaStream_t s) {
+                             unsigned* err, cudaStream_t s) {
   // persistent grid: the current device's SMs x resident blocks
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
+  CUtensorMap map;
+  if (err && records_tensor_map<VTYPE>(V, &map)) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_records_tma<VTYPE, OP>, 64, 0);
+    const int grid = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+    k_records_tma<VTYPE, OP><<<min(grid, nbricks), 64, 0, s>>>(V, need, list, rec, map, err);
+    return;
+  }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_records<VTYPE, OP>, 64, 0);
   const int grid = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
-  const int nbricks = V.nb[0] * V.nb[1] * V.nb[2];
   k_records<VTYPE, OP><<<min(grid, nbricks), 64, 0, s>>>(V, need, list, rec);
 }
 
 template <int VTYPE>
 static void launch_records_op(const VolDev& V, int op, const uint8_t* need, const int* list,
-                              float4* rec, cudaStream_t s) {
+                              float4* rec, unsigned* err, cudaStream_t s) {
   switch (op) {
-    case OP_CENTRAL: launch_records_k<VTYPE, OP_CENTRAL>(V, need, list, rec, s); break;
-    case OP_SOBEL: launch_records_k<VTYPE, OP_SOBEL>(V, need, list, rec, s); break;
-    default: launch_records_k<VTYPE, OP_ZH>(V, need, list, rec, s);
+    case OP_CENTRAL: launch_records_k<VTYPE, OP_CENTRAL>(V, need, list, rec, err, s); break;
+    case OP_SOBEL: launch_records_k<VTYPE, OP_SOBEL>(V, need, list, rec, err, s); break;
+    default: launch_records_k<VTYPE, OP_ZH>(V, need, list, rec, err, s);
   }
 }
 
 cudaError_t launch_records(const VolDev& V, int dtype, int op, const uint8_t* need,
-                           const int* list, float4* rec, cudaStream_t s) {
+                           const int* list, float4* rec, cudaStream_t s, unsigned* err) {
   switch (dtype) {
-    case VT_U8: launch_records_op<VT_U8>(V, op, need, list, rec, s); break;
-    case VT_U16: launch_records_op<VT_U16>(V, op, need, list, rec, s); break;
-    case VT_F16: launch_records_op<VT_F16>(V, op, need, list, rec, s); break;
-    default: launch_records_op<VT_F32>(V, op, need, list, rec, s);
+    case VT_U8: launch_records_op<VT_U8>(V, op, need, list, rec, err, s); break;
+    case VT_U16: launch_records_op<VT_U16>(V, op, need, list, rec, err, s); break;
+    case VT_F16: launch_records_op<VT_F16>(V, op, need, list, rec, err, s); break;
+    default: launch_records_op<VT_F32>(V, op, need, list, rec, err, s);
   }
   return cudaGetLastError();
 }

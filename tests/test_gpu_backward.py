@@ -374,3 +374,29 @@ def test_multi_view_backward_equals_sum_of_single_views(R):
     # a camera that does not match the recorded checkpoints is refused
     with pytest.raises(vr.VrError):
         vr.vr_render_backward_views(R.ctx, params, views[::-1], [c[1] for c in cks], grads, gv2, gt2)
+
+
+def test_adjoint_skips_only_rays_that_miss_the_box(R):
+    """The adjoint visits only the tiles of the box's screen rectangle: with the box off to
+    one side of a perspective view (most tiles outside it), the gradients still equal the
+    FP64 reverse mode element-wise (termination off, so both differentiate the same piece)."""
+    from paper_1609_01317_gb300 import vr
+
+    rng = np.random.default_rng(87)
+    shp = (14, 12, 10)
+    vol = rng.uniform(0.1, 0.9, (10, 12, 14)).astype(np.float32)
+    tf = P.tf_random(88, 16, alpha_max=0.2)
+    c, d = P.volume_centre(shp), P.volume_diag(shp)
+    cam = P.camera([c[0] + 1.6 * d, c[1] + 0.35 * d, c[2]], [c[0] + 0.3 * d, c[1] + 0.6 * d, c[2]],
+                   [0, 0, 1], 40, 24, fov_y_deg=50.0)
+    rect = vr.vr_screen_rect(cam, (0, 0, 0), [s - 1 for s in shp])
+    assert (rect[2] - rect[0]) * (rect[3] - rect[1]) < 0.6 * 40 * 24  # most tiles culled
+    wts = rng.uniform(-1, 1, (24, 40, 4))
+    params = vr.make_params(grad="sobel3d", skip_empty=False, ert_threshold=2.0)
+    img, gv, gt = gpu_grads(R, vol, tf, cam, params, wts)
+    assert (img[..., 3] > 0).sum() > 20
+    ref_v, ref_t = oracle.render_backward(oracle.OracleVolume(vol, 1.0), tf, cam,
+                                          oracle.make_params(grad="sobel3d", ert_threshold=2.0), wts)
+    okv, ev = elementwise_close(gv, ref_v)
+    okt, et = elementwise_close(gt, ref_t)
+    assert okv and okt, (ev, et)

@@ -372,10 +372,12 @@ def test_allocator_failure_is_reported_and_the_context_recovers():
 
 
 def test_screen_rectangle_culling_drops_no_ray():
-    """vr_render marches only the tiles of the sampling box's screen rectangle; a
-    checkpointed render marches every tile with the same arithmetic, so the two images must be
-    bit-identical for cameras that put the box anywhere: centred, partly off screen, filling
-    the view, around or inside the eye, wide and narrow fields of view, orthographic, clipped."""
+    """vr_render marches only the tiles of the sampling box's screen rectangle (and the adjoint
+    visits only that rectangle); a checkpointed render marches every tile with the same
+    arithmetic.  For cameras that put the box anywhere -- centred, partly off screen, filling
+    the view, around or inside the eye, wide and narrow fields of view, orthographic, clipped
+    -- the two images are bit-identical, every ray that the FP64 oracle marches has a non-zero
+    recorded end index (and every other ray 0), and the image matches the oracle's."""
     import torch
     from paper_1609_01317_gb300 import Renderer, build, vr
 
@@ -417,6 +419,12 @@ def test_screen_rectangle_culling_drops_no_ray():
                 vr.vr_render_forward_train(R.ctx, p, b, ck[off:off + nb], nb)
                 torch.cuda.synchronize()
                 assert torch.equal(a, b), f"camera {i}, clip {j}"
+                kend = ck[off:off + 4 * W * H].view(torch.int32).reshape(H, W).cpu().numpy()
+                ref, counts, _ = oracle.render(oracle.OracleVolume(vol, 4095.0),
+                                               P.tf_two_plateau(256), cam,
+                                               oracle.make_params(grad="sobel3d", **clip))
+                assert np.array_equal(kend > 0, counts > 0), f"camera {i}, clip {j}"
+                assert_image_parity(a.cpu().numpy(), ref, f"camera {i}, clip {j}")
                 lit += int((a[..., 3] > 0).sum().item() > 0)
         assert lit >= 14  # most views see the volume
     finally:
