@@ -211,10 +211,14 @@ def replica_throughput(samples_per_step, steps, step_ms_total, world):
 # ------------------------------------------------------------ ncu traffic record
 KERNEL_SOURCES = {
     "k_march": ["vr_device.cuh", "vr_internal.h", "vr_march.cuh", "vr_render.cu"],
+    "k_march_list": ["vr_device.cuh", "vr_internal.h", "vr_march.cuh", "vr_render.cu"],
+    "k_records_tma": ["vr_device.cuh", "vr_internal.h", "vr_volume.cu"],
     "k_adjoint": ["vr_device.cuh", "vr_internal.h", "vr_adjoint.cu"],
     "k_surface": ["vr_device.cuh", "vr_internal.h", "vr_surface.cu"],
 }
 PROFILE_SUMMARY = {"k_march": "profiles/k_march_ct512x512x361_1080p.md",
+                   "k_march_list": "profiles/k_march_list_vessels512_4k.md",
+                   "k_records_tma": "profiles/k_records_tma_ct512x512x361.md",
                    "k_adjoint": "profiles/k_adjoint_density128_16views.md",
                    "k_surface": "profiles/k_surface_ct512x512x361_1080p_bone.md"}
 
