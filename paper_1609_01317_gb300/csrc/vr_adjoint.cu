@@ -16,12 +16,15 @@
 // operator G at the cell corners, the kernel scatters (dL/ds, dL/dG) to the 8 corners
 // with one vector atomic each; a second, dense pass applies the transposed operator
 // stencil (with the clamp-to-edge folding) to turn dL/dG into dL/dV.
+#include <algorithm>
+
 #include "vr_internal.h"
 
 namespace vr {
 
 constexpr int kThreads = 128;
 constexpr int kMaxTfRows = 4096;  // per-block partial rows of the TF gradient up to this many entries
+constexpr int kMaxSharedTf = 1024;  // the block copies transfer functions up to this size to shared memory
 constexpr int kQuadTileW = 4, kQuadTileH = 2;  // pixels per warp (a quad of lanes per ray)
 
 // Corner records of a cell and the trilinear weights of the sample in it.
@@ -68,6 +71,37 @@ __device__ __forceinline__ float record_value(const RecDev& R, const AdjCell& c,
   return lerpf(lerpf(x00, x10, c.f[1]), lerpf(x01, x11, c.f[1]), c.f[2]);
 }
 
+// §3.7 lookup with linear interpolation between entries (the forward's tf_lookup), also
+// returning the difference of the two entries read: the slope of the table in u.
+template <bool SMEM>
+__device__ __forceinline__ TfSample tf_lookup_slope(const TfDev& tf, const float4* s_tf,
+                                                    float s_raw, float4& dab) {
+  TfSample r;
+  float u = s_raw * tf.scale;
+  const float top = (float)(tf.n - 1);
+  r.inside = (u >= 0.0f) && (u <= top);
+  u = fminf(fmaxf(u, 0.0f), top);
+  int i = (int)u;
+  if (i > tf.n - 2) i = tf.n - 2;
+  i = (int)VR_CHECK(tf.bounds, i, 0, tf.n - 2);
+  r.i = i;
+  r.w = u - (float)i;
+  float4 a, b;
+  if constexpr (SMEM) {
+    a = s_tf[i];
+    b = s_tf[i + 1];
+  } else {
+    a = __ldg(tf.tf + i);
+    b = __ldg(tf.tf + i + 1);
+  }
+  r.rgba.x = lerpf(a.x, b.x, r.w);
+  r.rgba.y = lerpf(a.y, b.y, r.w);
+  r.rgba.z = lerpf(a.z, b.z, r.w);
+  r.rgba.w = lerpf(a.w, b.w, r.w);
+  dab = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+  return r;
+}
+
 __device__ __forceinline__ void flush_tf(float* dst, int i, const float lo[4], const float hi[4]) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -78,10 +112,11 @@ __device__ __forceinline__ void flush_tf(float* dst, int i, const float lo[4], c
 
 // Transmittance before sample kg, recomputed forward from the checkpoint of its
 // 32-sample segment (used when dividing back through a group would lose precision).
-__device__ __noinline__ float recompute_T(const AdjointLaunch& L, const float o[3],
-                                          const float d[3], float tn, int kg, int ray) {
+__device__ __noinline__ float recompute_T(const AdjointLaunch& L, const float* ck_T, int nrays,
+                                          const float o[3], const float d[3], float tn, int kg,
+                                          int ray) {
   const int s0 = (kg >> 5) << 5;
-  float T = s0 == 0 ? 1.0f : L.ck_T[(size_t)((s0 >> 5) - 1) * (L.cam.width * L.cam.height) + ray];
+  float T = s0 == 0 ? 1.0f : ck_T[(size_t)((s0 >> 5) - 1) * nrays + ray];
   for (int j = s0; j < kg; ++j) {
     const float t = fmaf((float)j + 0.5f, L.r.step, tn);
     float p[3];
@@ -111,46 +146,55 @@ __device__ __forceinline__ void flush_tf_row(float* row, int i, const float lo[4
 // re-anchored at every 32-sample checkpoint), and the adjoint of the transmittance follows
 // from a suffix scan of the affine maps Tadj -> alpha g.c + (1 - alpha) Tadj.  The group loop
 // runs the same number of times on every lane of the warp (quads whose ray is done idle).
-__global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
+template <bool SMEM>
+__global__ void __launch_bounds__(kThreads) k_adjoint(const __grid_constant__ AdjointLaunch L) {
+  // SMEM: the block reads the transfer function from its copy in shared memory
+  extern __shared__ float4 s_tf[];
+  if constexpr (SMEM) {
+    for (int i = threadIdx.x; i < L.tf.n; i += kThreads) s_tf[i] = __ldg(L.tf.tf + i);
+    __syncthreads();
+  }
   // TF contributions: summed in registers per run of samples that read the same pair of
   // entries; a finished run goes to this block's row of the partial sums in global memory
   // (vector reductions, no contention between blocks), or, without a partial-sum buffer,
   // straight to grad_tf with scalar atomics.
   const int tid = threadIdx.x;
-  float* tf_row = L.tf_partial ? L.tf_partial + (size_t)blockIdx.x * 4 * L.tf.n : nullptr;
-
   const int lane = tid & 31, q = lane & 3, qd = lane >> 2;
+  float* tf_row = L.tf_partial ? L.tf_partial + (size_t)blockIdx.x * 4 * L.tf.n : nullptr;
   const unsigned qmask = 0xFu << (lane & ~3);
-  const int W = L.cam.width, H = L.cam.height;
-  const int nrays = W * H;
-  // tiles covering the rectangle L.rect (the rays outside it miss the box: nothing to do)
-  const int rx1 = min(L.rect[2], W), ry1 = min(L.rect[3], H);
-  const int tx0 = L.rect[0] / kQuadTileW, ty0 = L.rect[1] / kQuadTileH;
-  const int tiles_x = (rx1 + kQuadTileW - 1) / kQuadTileW - tx0;
-  const int tiles = rx1 > L.rect[0] && ry1 > L.rect[1]
-                        ? tiles_x * ((ry1 + kQuadTileH - 1) / kQuadTileH - ty0) : 0;
   const float step = L.r.step;
   const float gs = L.r.gscale;
   for (;;) {
     int tile = 0;
     if (lane == 0) tile = (int)atomicAdd(L.tile_counter, 1u);
     tile = __shfl_sync(0xffffffffu, tile, 0);
-    if (tile >= tiles) break;
-    const int px = (tx0 + tile % tiles_x) * kQuadTileW + (qd & 3);
-    const int py = (ty0 + tile / tiles_x) * kQuadTileH + (qd >> 2);
+    if (tile >= L.tiles_total) break;
+    // the view of this tile: the last one whose first tile is <= tile
+    int lo = 0, hi = L.nviews;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (L.view[mid].tile0 <= tile) lo = mid;
+      else hi = mid;
+    }
+    const AdjView& vw = L.view[lo];
+    const int local = tile - vw.tile0;
+    const int W = vw.cam.width, H = vw.cam.height;
+    const int nrays = W * H;
+    const int px = (vw.tx0 + local % vw.tiles_x) * kQuadTileW + (qd & 3);
+    const int py = (vw.ty0 + local / vw.tiles_x) * kQuadTileH + (qd >> 2);
     const bool active = px < W && py < H;
     const int ray = py * W + px;
     float o[3], d[3], tn = 0.0f;
     int K = 0, kend = 0;
     if (active) {
-      ray_setup(L.cam, L.r.lo, L.r.hi, L.r.step, px, py, o, d, tn, K);
-      kend = min(max(L.ck_kend[ray], 0), K);
+      ray_setup(vw.cam, L.r.lo, L.r.hi, L.r.step, px, py, o, d, tn, K);
+      kend = min(max(vw.ck_kend[ray], 0), K);
     }
     float4 gr = make_float4(0.f, 0.f, 0.f, 0.f);
     float Tcur = 1.0f;
     if (kend > 0) {
-      gr = __ldg(L.grad_rgba + ray);
-      Tcur = L.ck_Tend[ray];
+      gr = __ldg(vw.grad_rgba + ray);
+      Tcur = vw.ck_Tend[ray];
     }
     float Tadj = -gr.w;
     const int ng = kend > 0 ? ((kend - 1) >> 2) + 1 : 0;  // groups of this quad's ray
@@ -171,6 +215,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
         AdjCell c;
         float4 r[8];
         TfSample ts;
+        float4 dab;  // tf[i + 1] - tf[i] of the sample's entries
         ShadeOut so;
         float gh[3] = {0.f, 0.f, 0.f};
         float sv[4] = {0.f, 0.f, 0.f, 0.f};  // (dL/ds, dL/dG) of this sample
@@ -180,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
           c = adj_cell(L.V, p);
-          ts = tf_lookup(L.tf, record_value(L.R, c, r));
+          ts = tf_lookup_slope<SMEM>(L.tf, s_tf, record_value(L.R, c, r), dab);
           float g[3] = {0.f, 0.f, 0.f};
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -191,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
           }
 #pragma unroll
           for (int a = 0; a < 3; ++a) gh[a] = g[a] * gs;
-          shade(L.r.sh, L.cam, d, p, gh, ts.rgba, so);
+          shade(L.r.sh, vw.cam, d, p, gh, ts.rgba, so);
           alpha = ts.rgba.w;
           gc = gr.x * so.c[0] + gr.y * so.c[1] + gr.z * so.c[2];
         }
@@ -207,9 +252,9 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
         const float prod = __shfl_sync(qmask, P, 3, 4);
         float Tb;
         if (kg == 0) Tb = 1.0f;
-        else if ((kg & (kCkptStride - 1)) == 0) Tb = L.ck_T[(size_t)((kg >> 5) - 1) * nrays + ray];
+        else if ((kg & (kCkptStride - 1)) == 0) Tb = vw.ck_T[(size_t)((kg >> 5) - 1) * nrays + ray];
         else if (prod > 1e-4f) Tb = Tcur / prod;
-        else Tb = recompute_T(L, o, d, tn, kg, ray);
+        else Tb = recompute_T(L, vw.ck_T, nrays, o, d, tn, kg, ray);
         const float Tk = Tb * E;
         // adjoint of T: suffix scan of x -> A + B x over the group
         float A = alpha * gc, B = om;
@@ -267,9 +312,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const AdjointLaunch L) {
           // transfer-function backward: the slope to the value here, the entries below
           float ds = 0.0f;
           if (ts.inside) {
-            const float4 ta4 = __ldg(L.tf.tf + ts.i), tb4 = __ldg(L.tf.tf + ts.i + 1);
-            ds = (drgba[0] * (tb4.x - ta4.x) + drgba[1] * (tb4.y - ta4.y) +
-                  drgba[2] * (tb4.z - ta4.z) + drgba[3] * (tb4.w - ta4.w)) * L.tf.scale;
+            ds = (drgba[0] * dab.x + drgba[1] * dab.y + drgba[2] * dab.z + drgba[3] * dab.w) *
+                 L.tf.scale;
           }
           contrib = L.grad_tf != nullptr;
           ci = ts.i;
@@ -367,18 +411,46 @@ cudaError_t launch_tf_partial_reduce(const float* partial, int blocks, int n4, f
 
 bool adjoint_tf_rows(int ntf) { return ntf <= kMaxTfRows; }
 
-int adjoint_grid() {
+static bool tf_shared(int ntf) { return ntf <= kMaxSharedTf; }
+
+int adjoint_grid(int ntf) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint, kThreads, 0);
+  if (tf_shared(ntf))
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint<true>, kThreads,
+                                                  (size_t)ntf * sizeof(float4));
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint<false>, kThreads, 0);
   return (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
 }
 
+void adjoint_add_view(AdjointLaunch& L, const CamDev& cam, const int rect[4], const int* ck_kend,
+                      const float* ck_T, const float* ck_Tend, const float4* grad_rgba) {
+  AdjView& v = L.view[L.nviews++];
+  v.cam = cam;
+  v.ck_kend = ck_kend;
+  v.ck_T = ck_T;
+  v.ck_Tend = ck_Tend;
+  v.grad_rgba = grad_rgba;
+  const int rx1 = std::min(rect[2], cam.width), ry1 = std::min(rect[3], cam.height);
+  v.tx0 = rect[0] / kQuadTileW;
+  v.ty0 = rect[1] / kQuadTileH;
+  v.tiles_x = (rx1 + kQuadTileW - 1) / kQuadTileW - v.tx0;
+  const int tiles = rx1 > rect[0] && ry1 > rect[1]
+                        ? v.tiles_x * ((ry1 + kQuadTileH - 1) / kQuadTileH - v.ty0) : 0;
+  v.tile0 = L.tiles_total;
+  L.tiles_total += tiles;
+}
+
 cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t s) {
+  if (L.tiles_total == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  k_adjoint<<<adjoint_grid(), kThreads, 0, s>>>(L);
+  if (tf_shared(L.tf.n))
+    k_adjoint<true><<<adjoint_grid(L.tf.n), kThreads, (size_t)L.tf.n * sizeof(float4), s>>>(L);
+  else
+    k_adjoint<false><<<adjoint_grid(L.tf.n), kThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -402,44 +474,66 @@ __device__ __forceinline__ float tap_weight(int along, int b, int c) {
   (void)along;
 }
 
+// acc += the transposed taps that reach m's operator from the grid points j = m - o (CHECK:
+// skip j outside the grid; without it every j must lie inside).
+template <int OP, bool CHECK>
+__device__ __forceinline__ float add_transposed_taps(const float4* __restrict__ adj, const int m[3],
+                                                     int nx, int ny, int nz, float acc) {
+#pragma unroll
+  for (int oz = -1; oz <= 1; ++oz)
+#pragma unroll
+    for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+      for (int ox = -1; ox <= 1; ++ox) {
+        // signed weights of the three components' taps at offset (ox, oy, oz): the x
+        // component's tap has ox = +-1 and (b, c) = (oy, oz), and so on; offsets where all
+        // three vanish (every one but the six axis neighbours for central differences) are
+        // dropped when the loops unroll
+        const float wx = ox != 0 ? (float)ox * tap_weight<OP>(0, oy, oz) : 0.0f;
+        const float wy = oy != 0 ? (float)oy * tap_weight<OP>(1, oz, ox) : 0.0f;
+        const float wz = oz != 0 ? (float)oz * tap_weight<OP>(2, ox, oy) : 0.0f;
+        if (wx == 0.0f && wy == 0.0f && wz == 0.0f) continue;
+        const int j[3] = {m[0] - ox, m[1] - oy, m[2] - oz};
+        if (CHECK && (j[0] < 0 || j[0] >= nx || j[1] < 0 || j[1] >= ny || j[2] < 0 || j[2] >= nz))
+          continue;
+        const float4 aj = __ldg(adj + (j[0] + nx * (j[1] + ny * j[2])));
+        if (wx != 0.0f) acc += wx * aj.y;
+        if (wy != 0.0f) acc += wy * aj.z;
+        if (wz != 0.0f) acc += wz * aj.w;
+      }
+  return acc;
+}
+
 template <int OP>
-__global__ void k_adjoint_volume(const float4* __restrict__ adj, int nx, int ny, int nz,
-                                 float* __restrict__ gvol) {
-  const long nvox = (long)nx * ny * nz;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_adjoint_volume(const float4* __restrict__ adj, int nx,
+                                                        int ny, int nz, float* __restrict__ gvol) {
+  // the grid holds fewer than 2^31 voxels (checked at upload)
+  const int nvox = nx * ny * nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nvox) return;
-  const int v[3] = {(int)(i % nx), (int)((i / nx) % ny), (int)(i / ((long)nx * ny))};
-  const int n[3] = {nx, ny, nz};
+  const int v[3] = {i % nx, (i / nx) % ny, i / (nx * ny)};
   float acc = __ldg(&adj[i].x);
-  // candidate m per axis: v itself, and the border cells that clamp onto v
-  int mlist[3][3], mcnt[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    mcnt[a] = 0;
-    mlist[a][mcnt[a]++] = v[a];
-    if (v[a] == 0) mlist[a][mcnt[a]++] = -1;
-    if (v[a] == n[a] - 1) mlist[a][mcnt[a]++] = n[a];
+  if (v[0] > 0 && v[0] < nx - 1 && v[1] > 0 && v[1] < ny - 1 && v[2] > 0 && v[2] < nz - 1) {
+    // inside: only m = v clamps onto v, and all of its taps' grid points exist
+    gvol[i] += add_transposed_taps<OP, false>(adj, v, nx, ny, nz, acc);
+    return;
   }
-  for (int iz = 0; iz < mcnt[2]; ++iz)
-    for (int iy = 0; iy < mcnt[1]; ++iy)
-      for (int ix = 0; ix < mcnt[0]; ++ix) {
-        const int m[3] = {mlist[0][ix], mlist[1][iy], mlist[2][iz]};
-#pragma unroll
-        for (int oz = -1; oz <= 1; ++oz)
-#pragma unroll
-          for (int oy = -1; oy <= 1; ++oy)
-#pragma unroll
-            for (int ox = -1; ox <= 1; ++ox) {
-              if (ox == 0 && oy == 0 && oz == 0) continue;
-              const int j[3] = {m[0] - ox, m[1] - oy, m[2] - oz};
-              if (j[0] < 0 || j[0] >= nx || j[1] < 0 || j[1] >= ny || j[2] < 0 || j[2] >= nz)
-                continue;
-              const float4 aj = __ldg(adj + ((long)j[0] + (long)nx * ((long)j[1] + (long)ny * j[2])));
-              // x component: tap offset (ox, oy, oz) with ox = +-1, (b, c) = (oy, oz)
-              if (ox != 0) acc += (float)ox * tap_weight<OP>(0, oy, oz) * aj.y;
-              if (oy != 0) acc += (float)oy * tap_weight<OP>(1, oz, ox) * aj.z;
-              if (oz != 0) acc += (float)oz * tap_weight<OP>(2, ox, oy) * aj.w;
-            }
+  // candidate m per axis: v itself (bit 0), and the border cells that clamp onto v: -1 when
+  // v = 0 (bit 1), n when v = n - 1 (bit 2)
+  const unsigned mkx = 1u | (v[0] == 0 ? 2u : 0u) | (v[0] == nx - 1 ? 4u : 0u);
+  const unsigned mky = 1u | (v[1] == 0 ? 2u : 0u) | (v[1] == ny - 1 ? 4u : 0u);
+  const unsigned mkz = 1u | (v[2] == 0 ? 2u : 0u) | (v[2] == nz - 1 ? 4u : 0u);
+#pragma unroll 1
+  for (int iz = 0; iz < 3; ++iz)
+#pragma unroll 1
+    for (int iy = 0; iy < 3; ++iy)
+#pragma unroll 1
+      for (int ix = 0; ix < 3; ++ix) {
+        if (!((mkx >> ix) & (mky >> iy) & (mkz >> iz) & 1u)) continue;
+        const int m[3] = {v[0] + (ix == 0 ? 0 : (ix == 1 ? -1 : 1)),
+                          v[1] + (iy == 0 ? 0 : (iy == 1 ? -1 : 1)),
+                          v[2] + (iz == 0 ? 0 : (iz == 1 ? -1 : 1))};
+        acc = add_transposed_taps<OP, true>(adj, m, nx, ny, nz, acc);
       }
   gvol[i] += acc;
 }

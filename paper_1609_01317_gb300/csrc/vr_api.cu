@@ -822,7 +822,7 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
   }
   // transfer-function gradient: per-block partial sums, reduced once after all views
   const bool tf_partial = grad_tf && adjoint_tf_rows(ctx->ntf);
-  const int ablocks = adjoint_grid();
+  const int ablocks = adjoint_grid(ctx->ntf);
   if (tf_partial) {
     const size_t pbytes = (size_t)ablocks * 4 * ctx->ntf * sizeof(float);
     void* pp = ctx->tf_partial;
@@ -837,33 +837,36 @@ vr_status vr_render_backward_views(vr_ctx* ctx, const vr_render_params* params, 
   all.skip_empty = 0;
   st = ensure_records(ctx, &all, s);
   if (st != VR_OK) return st;
+  // the views' tiles form one work queue per launch of up to kAdjViews views
+  AdjointLaunch L;
+  L.V = vol_dev(ctx);
+  L.R = rec_dev(ctx);
+  L.tf = tf_dev(ctx);
+  L.r = render_dev(ctx, params);
+  L.dtype = (int)ctx->dtype;
+  L.op = params->grad;
+  L.tile_counter = reinterpret_cast<unsigned*>(ctx->stats + 5);
+  L.adj = grad_volume ? ctx->adj : nullptr;
+  L.grad_tf = grad_tf;
+  L.tf_partial = tf_partial ? ctx->tf_partial : nullptr;
   for (int v = 0; v < nviews; ++v) {
     const CkptRecord* rec = recs[v];
     CamDev basis;
     st = check_camera(&cams[v], &basis);
     if (st != VR_OK) return st;
-    AdjointLaunch L;
-    L.V = vol_dev(ctx);
-    L.R = rec_dev(ctx);
-    L.tf = tf_dev(ctx);
-    L.cam = basis;
-    L.r = render_dev(ctx, params);
-    L.dtype = (int)ctx->dtype;
-    L.op = params->grad;
-    L.ck_kend = static_cast<const int*>(checkpoints[v]);
-    L.ck_Tend = reinterpret_cast<const float*>(static_cast<const char*>(checkpoints[v]) +
-                                               align256((size_t)rec->nrays * 4));
-    L.ck_T = reinterpret_cast<const float*>(static_cast<const char*>(checkpoints[v]) +
-                                            2 * align256((size_t)rec->nrays * 4));
-    L.tile_counter = reinterpret_cast<unsigned*>(ctx->stats + 5);
-    L.nslots = rec->nslots;
-    L.grad_rgba = reinterpret_cast<const float4*>(grad_rgba[v]);
-    L.adj = grad_volume ? ctx->adj : nullptr;
-    L.grad_tf = grad_tf;
-    L.tf_partial = tf_partial ? ctx->tf_partial : nullptr;
-    screen_rect(basis, L.r.lo, L.r.hi, L.rect);  // rays outside it recorded end index 0
-    st = cuda_status(launch_adjoint(L, s));
-    if (st != VR_OK) return st;
+    const char* ck = static_cast<const char*>(checkpoints[v]);
+    int rect[4];
+    screen_rect(basis, L.r.lo, L.r.hi, rect);  // rays outside it recorded end index 0
+    adjoint_add_view(L, basis, rect, reinterpret_cast<const int*>(ck),
+                     reinterpret_cast<const float*>(ck + 2 * align256((size_t)rec->nrays * 4)),
+                     reinterpret_cast<const float*>(ck + align256((size_t)rec->nrays * 4)),
+                     reinterpret_cast<const float4*>(grad_rgba[v]));
+    if (L.nviews == kAdjViews || v == nviews - 1) {
+      st = cuda_status(launch_adjoint(L, s));
+      if (st != VR_OK) return st;
+      L.nviews = 0;
+      L.tiles_total = 0;
+    }
   }
   if (tf_partial) {
     st = cuda_status(launch_tf_partial_reduce(ctx->tf_partial, ablocks, 4 * ctx->ntf, grad_tf, s));

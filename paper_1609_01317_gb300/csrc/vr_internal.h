@@ -231,33 +231,47 @@ cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s);
 // misses the box [lo, hi] (the full image when that cannot be shown, empty for an empty box).
 void screen_rect(const CamDev& c, const float lo[3], const float hi[3], int rect[4]);
 
+// One view of an adjoint launch: its camera, the checkpoints its forward recorded, the
+// gradient of its image, and the tiles of its work in the launch's queue.
+struct AdjView {
+  CamDev cam;
+  const int* ck_kend;
+  const float* ck_T;
+  const float* ck_Tend;
+  const float4* grad_rgba;
+  // the warp tiles of the pixel rectangle [rect[0], rect[2]) x [rect[1], rect[3]) (every ray
+  // outside it misses the sampling box: its recorded end index is 0): tiles_x per row from
+  // tile (tx0, ty0), numbered from tile0 in the launch's queue
+  int tx0, ty0, tiles_x, tile0;
+};
+// views per adjoint launch (the descriptors travel in the launch's parameters)
+constexpr int kAdjViews = 16;
+
 struct AdjointLaunch {
   VolDev V;
   RecDev R;
   TfDev tf;
-  CamDev cam;
   RenderDev r;
   int dtype, op;
-  const int* ck_kend;
-  const float* ck_T;
-  const float* ck_Tend;
   unsigned* tile_counter;  // work counter of the persistent launch (zeroed per launch)
-  int nslots;
-  const float4* grad_rgba;
   float4* adj;     // per voxel corner accumulators (dL/ds, dL/dG) over the unpadded grid
   float* grad_tf;  // n x 4, accumulated
-  // when non-null: [adjoint_grid()][4 n] per-block sums of the TF gradient, added to with
+  // when non-null: [adjoint_grid(n)][4 n] per-block sums of the TF gradient, added to with
   // vector reductions; grad_tf then receives them through launch_tf_partial_reduce instead
   // of from the kernel
   float* tf_partial;
-  // pixels [rect[0], rect[2]) x [rect[1], rect[3]) whose tiles the launch visits; every ray
-  // outside misses the sampling box (its recorded end index is 0)
-  int rect[4] = {0, 0, 1 << 30, 1 << 30};
+  // the queue: the tiles of view[0], then those of view[1], ...
+  int nviews = 0, tiles_total = 0;
+  AdjView view[kAdjViews];
 };
+static_assert(sizeof(AdjointLaunch) <= 4096, "adjoint launch parameters exceed 4 KiB");
+// Appends a view to L's queue: the tiles of the rectangle rect of its image.
+void adjoint_add_view(AdjointLaunch& L, const CamDev& cam, const int rect[4], const int* ck_kend,
+                      const float* ck_T, const float* ck_Tend, const float4* grad_rgba);
 // whether the TF gradient goes through per-block partial rows for a table of ntf entries,
-// and the persistent grid the adjoint launches
+// and the persistent grid the adjoint launches for it
 bool adjoint_tf_rows(int ntf);
-int adjoint_grid();
+int adjoint_grid(int ntf);
 cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t s);
 // grad_tf[e] += sum over blocks b of partial[b][e], e < n4, in block order
 cudaError_t launch_tf_partial_reduce(const float* partial, int blocks, int n4, float* grad_tf,
