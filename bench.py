@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / cpu legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--leg", choices=["main", "fwd_bwd", "batch", "surface", "adaptive", "train",
-                                      "f16", "sparse"],
+                                      "f16", "sparse", "slab"],
                     default="main",
                     help="run one leg alone and print its JSON (for profiling)")
     ap.add_argument("--source-hash", choices=sorted(KERNEL_SOURCES),
@@ -212,9 +212,11 @@ def replica_throughput(samples_per_step, steps, step_ms_total, world):
 KERNEL_SOURCES = {
     "k_march": ["vr_device.cuh", "vr_internal.h", "vr_march.cuh", "vr_render.cu"],
     "k_march_list": ["vr_device.cuh", "vr_internal.h", "vr_march.cuh", "vr_render.cu"],
-    "k_records_tma": ["vr_device.cuh", "vr_internal.h", "vr_volume.cu"],
+    "k_records_tma": ["vr_device.cuh", "vr_internal.h", "vr_records.cuh", "vr_volume.cu"],
     "k_adjoint": ["vr_device.cuh", "vr_internal.h", "vr_adjoint.cu"],
     "k_surface": ["vr_device.cuh", "vr_internal.h", "vr_surface.cu"],
+    "k_march_slab": ["vr_device.cuh", "vr_internal.h", "vr_march.cuh", "vr_records.cuh",
+                     "vr_slab.cu"],
 }
 PROFILE_SUMMARY = {"k_march": "profiles/k_march_ct512x512x361_1080p.md",
                    "k_march_list": "profiles/k_march_list_vessels512_4k.md",
@@ -823,6 +825,70 @@ def sparse_leg(args, K):
             "voxels_nonzero_frac": float((vol > 0).mean())}
 
 
+def slab_leg(args, K):
+    """The two plain marches on the CT frame (1920 x 1080, Zucker-Hummel, skipping +
+    termination): the record march (gradient records of the visible bricks in device memory,
+    tile march) and the slab march (each 16 x 16 tile stages the raw voxels it crosses and
+    their records in shared memory, no record table).  Times the whole step (upload + TF +
+    camera + render, records recomputed) and the render alone, and checks that the two
+    frames are identical."""
+    import torch
+
+    import phantoms as P
+    from paper_1609_01317_gb300 import Renderer, vr
+
+    w = P.workload_ct()
+    vol = w["volume"]
+    nz, ny, nx = vol.shape
+    cam = w["camera"]
+    H, W = cam["height"], cam["width"]
+    R = Renderer(torch.cuda.current_device())
+    ctx = R.ctx
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream or None
+    vdev = torch.from_numpy(vol.view(np.int16)).cuda()
+    tdev = torch.from_numpy(w["tf"]).cuda()
+    cam_s = vr.make_camera(cam)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"workload": w["name"]}
+    frames = []
+    for march in ("records", "slabs"):
+        params = vr.make_params(step=w["step"], grad=w["grad"], skip_empty=True, march=march)
+        img = torch.empty((H, W, 4), device="cuda")
+
+        def step(p=params, img=img):
+            vr.vr_upload_volume(ctx, vdev, "u16", nx, ny, nz, w["value_max"], sh)
+            vr.vr_set_transfer_function(ctx, tdev, tdev.shape[0], sh)
+            vr.vr_set_camera(ctx, cam_s)
+            vr.vr_render(ctx, p, img, sh)
+
+        step(vr.make_params(step=w["step"], grad=w["grad"], skip_empty=True, march=march,
+                            collect_stats=True))
+        st = vr.vr_read_stats(ctx, sh)
+        for _ in range(3):
+            step()
+
+        def timed(fn):
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+            for i in range(K):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                fn()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+        out[march] = {"ms_per_step": timed(step),
+                      "render_ms": timed(lambda p=params, img=img: vr.vr_render(ctx, p, img, sh)),
+                      "march_ran": {1: "records", 2: "slabs"}.get(st["march"], "?"),
+                      "samples_visited": st["samples_visited"]}
+        frames.append(img)
+    out["identical"] = bool(torch.equal(frames[0], frames[1]))
+    out["samples_plain"] = st["samples_plain"]
+    R.close()
+    return out
+
+
 def run_sortfirst(args):
     """One frame of the workload split by rows over the ranks (sort-first, §2.2: rays are
     independent): every rank uploads the volume and renders its band of the busy rows
@@ -1067,6 +1133,7 @@ def run_ours(args):
     if not args.no_extras:
         line["f16"], f16_img, f16_vol = f16_leg(args, max(10, min(K, 50)))
         line["sparse"] = sparse_leg(args, max(10, min(K, 50)))
+        line["slab"] = slab_leg(args, max(10, min(K, 30)))
         line["train"] = train_leg(R, args)
         line["fwd_bwd"] = fwd_bwd_leg(R, args)
         line["surface"] = surface_leg(R, args)
@@ -1237,6 +1304,8 @@ def run_leg(args):
     elif args.leg == "sparse":
         out = sparse_leg(args, max(10, min(args.steps, 50)))
         out.pop("_samples", None)
+    elif args.leg == "slab":
+        out = slab_leg(args, max(10, min(args.steps, 50)))
     else:
         out = batch_leg(args)
         out.pop("_samples", None)

@@ -114,7 +114,23 @@ typedef struct {
      * samples taken (samples_visited). */
     int adaptive;
     float adapt_range2, adapt_range4;
+    /* Which march a plain render (vr_render / vr_render_rows without adaptive sampling) runs;
+     * every choice gives the same image bit for bit:
+     *   VR_MARCH_AUTO (0)    as RECORDS (the faster of the two on every workload measured);
+     *   VR_MARCH_RECORDS (1) the per-voxel gradient records of the visible bricks are
+     *                        computed into device memory (kept until the volume, operator
+     *                        or transfer function changes) and read by the tile march, or
+     *                        for sparse data by the ray-list march;
+     *   VR_MARCH_SLABS (2)   each 16 x 16 pixel tile walks the volume in slabs, staging the
+     *                        raw voxels it crosses and their records in shared memory (no
+     *                        record table in device memory), when the camera's rays lie
+     *                        close enough together for a tile's region to fit; else as
+     *                        RECORDS.  vr_read_stats reports which one ran.
+     * Other values: INVALID_ARG. */
+    int march;
 } vr_render_params;
+
+enum { VR_MARCH_AUTO = 0, VR_MARCH_RECORDS = 1, VR_MARCH_SLABS = 2 };
 
 /* Sample counters of the most recent render with collect_stats = 1. */
 typedef struct {
@@ -123,6 +139,8 @@ typedef struct {
                                         /* t_k up to early termination, skipped or not */
     unsigned long long samples_visited; /* samples actually interpolated               */
     unsigned long long samples_shaded;  /* samples with opacity != 0 (gradient+Phong)  */
+    unsigned long long march;           /* the march that rendered it: VR_MARCH_RECORDS */
+                                        /* or VR_MARCH_SLABS                            */
 } vr_stats;
 
 /* Device allocator callback pair: alloc returns device memory aligned to 256 bytes or

@@ -210,6 +210,7 @@ vr_status check_params(const vr_render_params* p) {
     if (std::isnan(p->clip_lo[a]) || std::isnan(p->clip_hi[a])) return VR_ERR_INVALID_ARG;
   if (p->adaptive && (std::isnan(p->adapt_range2) || std::isnan(p->adapt_range4)))
     return VR_ERR_INVALID_ARG;
+  if (p->march < VR_MARCH_AUTO || p->march > VR_MARCH_SLABS) return VR_ERR_INVALID_ARG;
   return VR_OK;
 }
 
@@ -348,11 +349,9 @@ void screen_rect(const CamDev& c, const float lo[3], const float hi[3], int rect
 static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* out,
                                int* ck_kend, float* ck_T, int nslots, cudaStream_t s,
                                float* ck_Tend = nullptr, int row0 = 0, int row1 = -1) {
-  vr_status rst = ensure_records(ctx, p, s);
-  if (rst != VR_OK) return rst;
   MarchLaunch L;
   L.V = vol_dev(ctx);
-  L.R = rec_dev(ctx);
+  L.R = rec_dev(ctx);  // refreshed below when the records are computed
   L.tf = tf_dev(ctx);
   L.cam = ctx->camdev;
   L.r = render_dev(ctx, p);
@@ -387,7 +386,22 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
       if (st != VR_OK) return st;
     }
   }
-  if (!ck_kend && !p->adaptive && L.rect[2] > L.rect[0]) {
+  // a plain render marches in slabs (no record table) when asked to and the camera allows
+  // it; the automatic choice is the record march, the faster one on every workload measured
+  bool slab = false;
+  if (!ck_kend && !p->adaptive && p->march == VR_MARCH_SLABS) {
+    vr_status st = ensure_hint(ctx);
+    if (st != VR_OK) return st;
+    L.hint = ctx->vis_hint_dev;
+    L.vis_count = ctx->brick_list;  // [0]: visible bricks
+    slab = slab_eligible(L);
+  }
+  if (!slab) {
+    const vr_status rst = ensure_records(ctx, p, s);
+    if (rst != VR_OK) return rst;
+    L.R = rec_dev(ctx);
+  }
+  if (!slab && !ck_kend && !p->adaptive && L.rect[2] > L.rect[0]) {
     // plain render: the rays of the rectangle's tiles are set up and listed first
     const size_t tiles = (size_t)((L.rect[2] + 3) / 4 - L.rect[0] / 4) *
                          (size_t)((L.rect[3] + 1) / 2 - L.rect[1] / 2);
@@ -417,8 +431,11 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
     if (st != VR_OK) return st;
     L.r.mult = static_cast<const uint8_t*>(ctx->adapt_mult);
   }
-  const vr_status st = cuda_status(launch_march(L, s));
-  if (st == VR_OK) ctx->stats_valid = ctx->stats_valid || p->collect_stats;
+  const vr_status st = cuda_status(slab ? launch_march_slab(L, s) : launch_march(L, s));
+  if (st == VR_OK && p->collect_stats) {
+    ctx->stats_valid = true;
+    ctx->stats_march = slab ? VR_MARCH_SLABS : VR_MARCH_RECORDS;
+  }
   return st;
 }
 
@@ -904,6 +921,7 @@ vr_status vr_read_stats(vr_ctx* ctx, vr_stats* out, void* stream) {
   out->samples_plain = h[1];
   out->samples_visited = h[2];
   out->samples_shaded = h[3];
+  out->march = (unsigned long long)ctx->stats_march;
   return VR_OK;
 }
 

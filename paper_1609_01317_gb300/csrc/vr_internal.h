@@ -82,6 +82,7 @@ struct vr_ctx {
   // timeout word [8] (16 slots)
   unsigned long long* stats = nullptr;
   bool stats_valid = false;
+  int stats_march = 0;  // VR_MARCH_RECORDS / VR_MARCH_SLABS of the render the counters are from
 
   // output staging for host destinations
   void* out_staging = nullptr;
@@ -227,6 +228,10 @@ struct MarchLaunch {
   int* hint = nullptr;  // host-mapped {count, bricks}: written by the march for the next render
 };
 cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s);
+// The slab march (no record table): whether it can render L (a plain render whose rays lie
+// close enough together), and its launch.
+bool slab_eligible(const MarchLaunch& L);
+cudaError_t launch_march_slab(const MarchLaunch& L, cudaStream_t s);
 // Pixel rectangle [rect[0], rect[2]) x [rect[1], rect[3]) outside which every ray of camera c
 // misses the box [lo, hi] (the full image when that cannot be shown, empty for an empty box).
 void screen_rect(const CamDev& c, const float lo[3], const float hi[3], int rect[4]);

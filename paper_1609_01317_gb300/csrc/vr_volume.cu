@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "vr_internal.h"
+#include "vr_records.cuh"
 
 namespace vr {
 
@@ -327,107 +328,6 @@ namespace vr {
 // upper face it lies on (several such bricks write the same value).  Per brick the 11^3
 // clamp-to-edge neighbourhood [8b-1, 8b+9]^3 is staged in shared memory, then the (x, y)
 // columns of records are streamed along z (see k_records).
-// Sums of one z plane of a voxel's 3x3x3 neighbourhood (pl[y][x], the voxel at [w+1][u+1])
-// from which the operators of §3.5 are assembled.  Every 3x3x3 operator here weights a tap
-// by its class only: centre w0, edge w1, corner w2 of the 3x3 mask across the component's
-// axis.  With d_x(b) the difference along x in row b of the plane, and likewise d_y(a):
-//   ax = d_x(0), bx = d_x(-1) + d_x(+1), ay = d_y(0), by = d_y(-1) + d_y(+1),
-//   q  = the plane weighted by the mask (for the z component), c = the voxel's own value.
-// G_x = w0 ax(z) + w1 (bx(z) + ax(z-1) + ax(z+1)) + w2 (bx(z-1) + bx(z+1)), G_y likewise,
-// G_z = q(z+1) - q(z-1); central differences use ax, ay and c only.
-struct PlaneSums {
-  float ax, bx, ay, by, q, c;
-};
-
-template <int OP>
-__device__ __forceinline__ PlaneSums plane_sums(const float (*pl)[12], int u, int w) {
-  PlaneSums r;
-  if constexpr (OP == OP_CENTRAL) {
-    r.ax = pl[w + 1][u + 2] - pl[w + 1][u];
-    r.ay = pl[w + 2][u + 1] - pl[w][u + 1];
-    r.c = pl[w + 1][u + 1];
-    r.bx = r.by = r.q = 0.0f;
-  } else {
-    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
-    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
-    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
-    float p[3][3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) p[b][a] = pl[w + b][u + a];
-    r.ax = p[1][2] - p[1][0];
-    r.bx = (p[0][2] - p[0][0]) + (p[2][2] - p[2][0]);
-    r.ay = p[2][1] - p[0][1];
-    r.by = (p[2][0] - p[0][0]) + (p[2][2] - p[0][2]);
-    r.q = fmaf(w0, p[1][1], fmaf(w1, (p[0][1] + p[2][1]) + (p[1][0] + p[1][2]),
-                                 w2 * ((p[0][0] + p[0][2]) + (p[2][0] + p[2][2]))));
-    r.c = p[1][1];
-  }
-  return r;
-}
-
-// Plane sums of two neighbouring voxels (tile columns u + 1 and u + 2, rows w .. w + 2) from
-// one 3 x 4 patch read with 64-bit shared loads (u even); the two voxels share the patch's
-// column differences and sums along y.
-template <int OP>
-__device__ __forceinline__ void plane_sums2(const float (*pl)[12], int u, int w, PlaneSums& A,
-                                            PlaneSums& B) {
-  float p[3][4];
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const float2 lo = *reinterpret_cast<const float2*>(&pl[w + b][u]);
-    const float2 hi = *reinterpret_cast<const float2*>(&pl[w + b][u + 2]);
-    p[b][0] = lo.x;
-    p[b][1] = lo.y;
-    p[b][2] = hi.x;
-    p[b][3] = hi.y;
-  }
-  A.ax = p[1][2] - p[1][0];
-  B.ax = p[1][3] - p[1][1];
-  A.c = p[1][1];
-  B.c = p[1][2];
-  if constexpr (OP == OP_CENTRAL) {
-    A.ay = p[2][1] - p[0][1];
-    B.ay = p[2][2] - p[0][2];
-    A.bx = A.by = A.q = B.bx = B.by = B.q = 0.0f;
-  } else {
-    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
-    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
-    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
-    float dy[4], sy[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      dy[c] = p[2][c] - p[0][c];
-      sy[c] = p[0][c] + p[2][c];
-    }
-    A.bx = sy[2] - sy[0];
-    B.bx = sy[3] - sy[1];
-    A.ay = dy[1];
-    B.ay = dy[2];
-    A.by = dy[0] + dy[2];
-    B.by = dy[1] + dy[3];
-    A.q = fmaf(w0, p[1][1], fmaf(w1, sy[1] + (p[1][0] + p[1][2]), w2 * (sy[0] + sy[2])));
-    B.q = fmaf(w0, p[1][2], fmaf(w1, sy[2] + (p[1][1] + p[1][3]), w2 * (sy[1] + sy[3])));
-  }
-}
-
-// The record of a voxel from the plane sums below, at and above it.
-template <int OP>
-__device__ __forceinline__ float4 record_of(const PlaneSums& lo, const PlaneSums& md,
-                                            const PlaneSums& hi) {
-  if constexpr (OP == OP_CENTRAL) {
-    return make_float4(md.ax, md.ay, hi.c - lo.c, md.c);
-  } else {
-    constexpr float w0 = (OP == OP_SOBEL) ? 6.0f : 1.0f;
-    constexpr float w1 = (OP == OP_SOBEL) ? 3.0f : 0.70710678118654752f;
-    constexpr float w2 = (OP == OP_SOBEL) ? 1.0f : 0.57735026918962576f;
-    return make_float4(fmaf(w0, md.ax, fmaf(w1, md.bx + (lo.ax + hi.ax), w2 * (lo.bx + hi.bx))),
-                       fmaf(w0, md.ay, fmaf(w1, md.by + (lo.ay + hi.ay), w2 * (lo.by + hi.by))),
-                       hi.q - lo.q, md.c);
-  }
-}
-
 // Padded row (y0 - 1 + j, z0 - 1 + k) of brick (x0, y0, z0) from padded x = x0, i.e. voxels
 // x0 - 1 .. x0 + 14, as one aligned 16-element vector of raw words (row pitches are
 // multiples of 16 elements and x0 of 8; the vector ends inside the row); rows beyond n are
@@ -552,12 +452,12 @@ __global__ void __launch_bounds__(64) k_records(const VolDev V, const uint8_t* _
         if (ncol == 2) {
           const bool two = x + 1 < nx;
           PlaneSums A[3], B[3];
-          plane_sums2<OP>(tile[0], u, w, A[0], B[0]);
-          plane_sums2<OP>(tile[1], u, w, A[1], B[1]);
+          plane_sums2<OP, VTYPE == VT_U8 || VTYPE == VT_U16>(tile[0], u, w, A[0], B[0]);
+          plane_sums2<OP, VTYPE == VT_U8 || VTYPE == VT_U16>(tile[1], u, w, A[1], B[1]);
 #pragma unroll
           for (int q = 0; q <= kBrick; ++q) {
             if (q < qn) {
-              plane_sums2<OP>(tile[q + 2], u, w, A[(q + 2) % 3], B[(q + 2) % 3]);
+              plane_sums2<OP, VTYPE == VT_U8 || VTYPE == VT_U16>(tile[q + 2], u, w, A[(q + 2) % 3], B[(q + 2) % 3]);
               if (q < kBrick ? wr_lo : wr_top) {
                 out[VR_CHECK(V.bounds, q * zstride, -(long long)obase, olast - (long long)obase)] =
                     record_of<OP>(A[q % 3], A[(q + 1) % 3], A[(q + 2) % 3]);
@@ -750,12 +650,12 @@ __global__ void __launch_bounds__(64) k_records_tma(const VolDev V, const uint8_
         if (ncol == 2) {
           const bool two = x + 1 < nx;
           PlaneSums A[3], Bs[3];
-          plane_sums2<OP>(tile[0], u, w, A[0], Bs[0]);
-          plane_sums2<OP>(tile[1], u, w, A[1], Bs[1]);
+          plane_sums2<OP, VTYPE == VT_U8 || VTYPE == VT_U16>(tile[0], u, w, A[0], Bs[0]);
+          plane_sums2<OP, VTYPE == VT_U8 || VTYPE == VT_U16>(tile[1], u, w, A[1], Bs[1]);
 #pragma unroll
           for (int q = 0; q <= kBrick; ++q) {
             if (q < qn) {
-              plane_sums2<OP>(tile[q + 2], u, w, A[(q + 2) % 3], Bs[(q + 2) % 3]);
+              plane_sums2<OP, VTYPE == VT_U8 || VTYPE == VT_U16>(tile[q + 2], u, w, A[(q + 2) % 3], Bs[(q + 2) % 3]);
               if (q < kBrick ? wr_lo : wr_top) {
                 out[VR_CHECK(V.bounds, q * zstride, -(long long)obase, olast - (long long)obase)] =
                     record_of<OP>(A[q % 3], A[(q + 1) % 3], A[(q + 2) % 3]);

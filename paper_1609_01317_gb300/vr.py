@@ -40,7 +40,7 @@ class vr_render_params(C.Structure):
                 ("headlight", C.c_int), ("ert_threshold", C.c_float), ("skip_empty", C.c_int),
                 ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3),
                 ("collect_stats", C.c_int), ("adaptive", C.c_int),
-                ("adapt_range2", C.c_float), ("adapt_range4", C.c_float)]
+                ("adapt_range2", C.c_float), ("adapt_range4", C.c_float), ("march", C.c_int)]
 
 
 class vr_surface_params(C.Structure):
@@ -53,7 +53,8 @@ class vr_surface_params(C.Structure):
 
 class vr_stats(C.Structure):
     _fields_ = [("rays_hit", C.c_ulonglong), ("samples_plain", C.c_ulonglong),
-                ("samples_visited", C.c_ulonglong), ("samples_shaded", C.c_ulonglong)]
+                ("samples_visited", C.c_ulonglong), ("samples_shaded", C.c_ulonglong),
+                ("march", C.c_ulonglong)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -193,19 +194,24 @@ def make_camera(cam: dict) -> vr_camera:
                      int(cam["height"]))
 
 
+MARCHES = {"auto": 0, "records": 1, "slabs": 2}
+
+
 def make_params(step=0.5, grad="central", ka=0.1, kd=0.7, ks=0.2, shininess=20.0,
                 light=(0.0, 0.0, 0.0), headlight=True, ert_threshold=0.99, skip_empty=True,
                 clip_lo=(-1e30, -1e30, -1e30), clip_hi=(1e30, 1e30, 1e30),
-                collect_stats=False, adapt_range=None) -> vr_render_params:
+                collect_stats=False, adapt_range=None, march="auto") -> vr_render_params:
     """adapt_range = (bound of multiplier 2, bound of multiplier 4) in raw value units turns
-    adaptive sampling on (a negative bound disables its level); None = off."""
+    adaptive sampling on (a negative bound disables its level); None = off.  march: "auto",
+    "records" or "slabs" (the kernel a plain render runs; the same image either way)."""
     g = GRADS[grad] if isinstance(grad, str) else int(grad)
     ad = adapt_range is not None
     r2, r4 = (float(adapt_range[0]), float(adapt_range[1])) if ad else (-1.0, -1.0)
     return vr_render_params(float(step), g, float(ka), float(kd), float(ks), float(shininess),
                             (C.c_float * 3)(*light), int(bool(headlight)), float(ert_threshold),
                             int(bool(skip_empty)), (C.c_float * 3)(*clip_lo),
-                            (C.c_float * 3)(*clip_hi), int(bool(collect_stats)), int(ad), r2, r4)
+                            (C.c_float * 3)(*clip_hi), int(bool(collect_stats)), int(ad), r2, r4,
+                            MARCHES[march] if isinstance(march, str) else int(march))
 
 
 def make_surface_params(step=2.0, iso_lo=0.5, iso_hi=3.0e38, refine=6, grad="central", ka=0.1,
