@@ -222,7 +222,8 @@ PROFILE_SUMMARY = {"k_march": "profiles/k_march_ct512x512x361_1080p.md",
                    "k_march_list": "profiles/k_march_list_vessels512_4k.md",
                    "k_records_tma": "profiles/k_records_tma_ct512x512x361.md",
                    "k_adjoint": "profiles/k_adjoint_density128_16views.md",
-                   "k_surface": "profiles/k_surface_ct512x512x361_1080p_bone.md"}
+                   "k_surface": "profiles/k_surface_ct512x512x361_1080p_bone.md",
+                   "k_march_slab": "profiles/k_march_slab_ct512x512x361_1080p.md"}
 
 
 def source_hash(kernel):
