@@ -208,13 +208,13 @@ def test_gradients_match_finite_differences_and_fp64_reverse_mode_density_128(R)
         checked += 1
         r = abs(g - g64) / (REL * abs(g64) + FLOOR * scale64)
         an_ratio.append(r)
-        if r > 1.0:
+        if not r <= 1.0:  # a NaN derivative fails too
             failures.append(("vs FP64 reverse mode", kind, key, g, g64))
         fd, h = _fd_derivative(loss_at)
         if fd != 0.0 and abs(g64 - fd) <= 1e-4 * abs(fd):
             fd_refs += 1
             fd_rel.append(abs(g - fd) / abs(fd))
-            if fd_rel[-1] > 1e-3:
+            if not fd_rel[-1] <= 1e-3:
                 failures.append(("vs finite difference", kind, key, g, fd, h))
 
     for vi in (0, 9):
