@@ -171,3 +171,18 @@ def test_sparse_data_and_automatic_choice(R):
         torch.cuda.synchronize()
         assert R.stats()["march"] == 1
         assert torch.equal(img, res[0][0])
+
+
+def test_march_selector_is_validated(R):
+    from paper_1609_01317_gb300 import vr
+
+    w = P.workload_sphere_64()
+    R.upload_volume(w["volume"], 255.0)
+    R.set_transfer_function(w["tf"])
+    R.set_camera(w["camera"])
+    for bad in (-1, 3):
+        with pytest.raises(vr.VrError):
+            R.render(params=vr.make_params(march=bad))
+    # adaptive sampling runs the record march whatever is asked
+    R.render(params=vr.make_params(march="slabs", adapt_range=(400.0, 150.0), collect_stats=True))
+    assert R.stats()["march"] == 1
