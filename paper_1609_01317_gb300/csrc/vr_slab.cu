@@ -1,18 +1,24 @@
-// vr_slab.cu -- the plain march with the bricks each ray tile crosses staged in shared memory.
+// vr_slab.cu -- the plain march with the bricks each ray tile crosses staged in shared memory
+// (VR_MARCH_SLABS; the record march stays the default, being faster on every workload
+// measured).
 //
 // A block of 256 threads marches a 16 x 16 pixel tile of the box's screen rectangle, one ray
 // per thread.  The rays of a tile are nearly parallel, so they advance together along the
 // axis a on which every one of them moves fastest (all with the same sign): the block walks
-// the volume front to back in slabs of D cells along a (D set per launch).  Per slab:
-//   1. one block reduction finds the first slab any ray is still in and the cell range the
-//      rays' samples cover there (per ray: its first sample in the slab and one past its
-//      analytic exit, one cell of margin);
-//   2. the bricks of that region are looked up (§5.3): when none is visible, the rays only
-//      step their sample index through the slab;
+// the volume front to back in slabs along a -- 2^Ds cells of a fixed grid (Ds set per launch
+// from how far apart the rays are), or the single next cell where the coarse slab's region
+// would not fit in shared memory.  Per slab:
+//   0. each ray first jumps over transparent bricks, macro bricks and super bricks on its own
+//      (§5.3, §5.4; the samples passed over have zero opacity);
+//   1. one block reduction of packed keys finds the nearest slab any ray is still in and the
+//      cell range the rays' samples cover there (per ray: its next sample and one past its
+//      analytic exit of the slab, one cell of margin), for both slab sizes at once;
+//   2. the bricks of that region are looked up: when none is visible, the rays only step
+//      their sample index through the slab;
 //   3. otherwise the clamp-to-edge raw voxels of the region plus one voxel around it are
-//      staged in shared memory (coalesced rows), and the gradient record of every voxel of
-//      the region -- the operator gradient G and the value, §3.5 -- is computed there, with
-//      the same arithmetic as the records pass;
+//      staged in shared memory (every thread issuing several loads before storing them), and
+//      the gradient record of every voxel of the region -- the operator gradient G and the
+//      value, §3.5 -- is computed there with the records pass's arithmetic (vr_records.cuh);
 //   4. every ray marches its samples in the slab exactly as the tile march does: the sample
 //      at t_k = t_near + (k + 1/2) step, skipped when its brick is transparent, else the 8
 //      corner records of its cell (now from shared memory), trilinear value (§3.4),
