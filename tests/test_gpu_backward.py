@@ -203,7 +203,7 @@ def test_gradients_match_finite_differences_and_fp64_reverse_mode_density_128(R)
     tfd = tf.astype(np.float64).copy()
     failures, checked, fd_refs, flipped, fd_rel, an_ratio = [], 0, 0, 0, [], []
 
-    def judge(kind, key, g, g64, scale64, loss_at):
+    def check_param(kind, key, g, g64, scale64, loss_at):
         nonlocal checked, fd_refs
         checked += 1
         r = abs(g - g64) / (REL * abs(g64) + FLOOR * scale64)
@@ -244,7 +244,7 @@ def test_gradients_match_finite_differences_and_fp64_reverse_mode_density_128(R)
                 arr[idx] = x0
                 return v
 
-            judge("voxel", (vi, int(idx)), gv.ravel()[idx], ref_v.ravel()[idx], scale_v, loss_at)
+            check_param("voxel", (vi, int(idx)), gv.ravel()[idx], ref_v.ravel()[idx], scale_v, loss_at)
         # TF entries: 16 x 16-pixel windows of a 64 x 64 copy of the view whose rays end at
         # the same sample in FP32 and FP64; weights inside the window only
         small = dict(cam, width=64, height=64)
@@ -267,7 +267,7 @@ def test_gradients_match_finite_differences_and_fp64_reverse_mode_density_128(R)
                     t2[i, c] += dv
                     return _fd_loss(ov, t2, small, pr, wts_s, w)
 
-                judge("tf", (vi, w, int(i), int(c)), gts[i, c], ref_t[i, c], scale_t, loss_at)
+                check_param("tf", (vi, w, int(i), int(c)), gts[i, c], ref_t[i, c], scale_t, loss_at)
     fd_rel = np.array(fd_rel)
     print(f"R17 gradient check: {checked} parameters checked against the FP64 reverse mode "
           f"(worst {max(an_ratio):.2f} of the bound); {fd_refs} with a finite-difference "
