@@ -171,7 +171,9 @@ vr_status vr_upload_volume(vr_ctx *ctx, const void *voxels, vr_dtype dtype, int 
 /* Set the transfer function (§3.7 colour lookup table): n RGBA float32 entries in host or
  * device memory, entry i covering s = i / (n - 1), read with linear interpolation between
  * entries.  Values are used as given (no clamping of alpha).  Recomputes the per-brick
- * visibility flags when a volume is present.  Errors: INVALID_ARG (NULL, n < 2,
+ * visibility flags when a volume is present.  A host table is copied into pinned memory the
+ * context owns before the call returns, so the caller may reuse it at once; the call does
+ * not wait for the stream's earlier work.  Errors: INVALID_ARG (NULL, n < 2,
  * n > 65536), OUT_OF_MEMORY, CUDA; after OUT_OF_MEMORY or CUDA the context holds no transfer
  * function until a set succeeds. */
 vr_status vr_set_transfer_function(vr_ctx *ctx, const float *rgba, int n, void *stream);

@@ -518,6 +518,8 @@ void vr_destroy(vr_ctx* ctx) {
   ctx_free(ctx, ctx->brick_minmax);
   ctx_free(ctx, ctx->upload_staging);
   if (ctx->host_copy_done) cudaEventDestroy(ctx->host_copy_done);
+  if (ctx->tf_stage_done) cudaEventDestroy(ctx->tf_stage_done);
+  if (ctx->tf_host_stage) cudaFreeHost(ctx->tf_host_stage);
   if (ctx->vis_hint) cudaFreeHost(const_cast<int*>(ctx->vis_hint));
   ctx_free(ctx, ctx->tf);
   ctx_free(ctx, ctx->stats);
@@ -655,11 +657,39 @@ vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, void* 
   }
   ctx->tf_prefix = reinterpret_cast<int*>(static_cast<char*>(buf) + tfb);
   const bool dev = is_device_pointer(rgba);
-  st = cuda_status(cudaMemcpyAsync(ctx->tf, rgba, (size_t)n * sizeof(float4),
+  const size_t bytes = (size_t)n * sizeof(float4);
+  const void* src = rgba;
+  if (!dev) {
+    // a host table goes through the context's pinned staging: the caller's table is free as
+    // soon as it is copied there, and the call need not wait for the stream to reach the
+    // copy (behind, say, the upload of a volume); only the previous copy out of the staging
+    // must have finished before it is overwritten
+    if (ctx->tf_stage_done) {
+      st = cuda_status(cudaEventSynchronize(ctx->tf_stage_done));
+      if (st != VR_OK) return st;
+    } else {
+      st = cuda_status(cudaEventCreateWithFlags(&ctx->tf_stage_done, cudaEventDisableTiming));
+      if (st != VR_OK) return st;
+    }
+    if (ctx->tf_host_stage_cap < bytes) {
+      if (ctx->tf_host_stage) cudaFreeHost(ctx->tf_host_stage);
+      ctx->tf_host_stage = nullptr;
+      ctx->tf_host_stage_cap = 0;
+      st = cuda_status(cudaHostAlloc(&ctx->tf_host_stage, bytes, cudaHostAllocDefault));
+      if (st != VR_OK) {
+        ctx->tf_host_stage = nullptr;
+        return st;
+      }
+      ctx->tf_host_stage_cap = bytes;
+    }
+    std::memcpy(ctx->tf_host_stage, rgba, bytes);
+    src = ctx->tf_host_stage;
+  }
+  st = cuda_status(cudaMemcpyAsync(ctx->tf, src, bytes,
                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   if (st != VR_OK) return st;
   if (!dev) {
-    st = mark_host_copy(ctx, s);
+    st = cuda_status(cudaEventRecord(ctx->tf_stage_done, s));
     if (st != VR_OK) return st;
   }
   st = cuda_status(launch_tf_prefix(ctx->tf, n, ctx->tf_prefix, s));
@@ -667,10 +697,7 @@ vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, void* 
   ctx->ntf = n;
   ctx->has_tf = true;
   ++ctx->tf_gen;
-  st = refresh_visibility(ctx, s);
-  // the caller's host table has been read once the copy is done
-  if (st == VR_OK && !dev) st = cuda_status(cudaEventSynchronize(ctx->host_copy_done));
-  return st;
+  return refresh_visibility(ctx, s);
 }
 
 

@@ -62,6 +62,10 @@ struct vr_ctx {
   size_t brick_cap = 0;
   void* upload_staging = nullptr;
   cudaEvent_t host_copy_done = nullptr;  // end of the last copy from a caller's host buffer
+  // pinned staging of a host transfer function, and the end of the last copy out of it
+  void* tf_host_stage = nullptr;
+  size_t tf_host_stage_cap = 0;
+  cudaEvent_t tf_stage_done = nullptr;
   size_t upload_cap = 0;
 
   // transfer function

@@ -429,3 +429,34 @@ def test_screen_rectangle_culling_drops_no_ray():
         assert lit >= 14  # most views see the volume
     finally:
         R.close()
+
+
+def test_host_transfer_function_is_free_when_the_call_returns(R):
+    """A host table is staged by the call: overwriting it right after the call (before the
+    stream has run the upload queued ahead of it) does not change the frame."""
+    import torch
+    from paper_1609_01317_gb300 import vr
+
+    w = P.workload_ct(width=256, height=160, shape=(96, 96, 68))
+    vol = torch.from_numpy(w["volume"].view(np.int16)).cuda()
+    nz, ny, nx = w["volume"].shape
+    params = vr.make_params(step=0.5, grad="zucker_hummel")
+    cam = vr.make_camera(w["camera"])
+    out = torch.empty((160, 256, 4), device="cuda")
+    s = torch.cuda.Stream()
+    h = s.cuda_stream
+    frames = []
+    for clobber in (False, True):
+        table = np.ascontiguousarray(w["tf"], np.float32).copy()
+        with torch.cuda.stream(s):
+            torch.cuda._sleep(2_000_000)  # keep the stream busy so the copy is still queued
+            vr.vr_upload_volume(R.ctx, vol, "u16", nx, ny, nz, P.U12_MAX, h)
+            vr.vr_set_transfer_function(R.ctx, table, table.shape[0], h)
+            if clobber:
+                table[:] = 0.5  # a different table, written before the stream reaches the copy
+            vr.vr_set_camera(R.ctx, cam)
+            vr.vr_render(R.ctx, params, out, h)
+        s.synchronize()
+        frames.append(out.clone())
+    assert torch.equal(frames[0], frames[1])
+    assert frames[0][..., 3].max() > 0
