@@ -59,9 +59,10 @@ def parse():
                     help="print the source hash recorded beside a kernel's ncu counters")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="edge scale of the batched-render volumes (1.0 = full sizes)")
-    ap.add_argument("--mode", choices=["replicas", "sortfirst"], default="replicas",
-                    help="N > 1: independent replicas of the frame (weak scaling, default) or "
-                         "one frame split by rows over the ranks and gathered (strong)")
+    ap.add_argument("--mode", choices=["replicas", "sortfirst", "sortlast"], default="replicas",
+                    help="N > 1: independent replicas of the frame (weak scaling, default), "
+                         "one frame split by rows over the ranks and gathered, or one frame "
+                         "split by z slabs of the volume and composited (both strong)")
     return ap.parse_args()
 
 
@@ -968,6 +969,89 @@ def run_sortfirst(args):
     return 0
 
 
+def run_sortlast(args):
+    """One frame of the workload split by z slabs of the volume (sort-last: Eq. 6 is
+    associative): every rank holds the volume, composites the samples of its slab into a
+    partial image (vr_render_partial, whole-box sampling grid, no early termination), the
+    partial images are all-gathered over NCCL and composited front to back along each pixel's
+    ray on every rank.  Strong scaling: value = the frame's plain samples (without early
+    termination) / the slowest rank's step time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1609_01317_gb300 import Renderer, build, sortlast as SL, vr
+
+    rank, world, local = dist_setup(args)
+    build.build()
+    w = workload(args.workload)
+    vol = w["volume"]
+    nz, ny, nx = vol.shape
+    dt = dtype_name(vol)
+    cam = w["camera"]
+    H, W = cam["height"], cam["width"]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream or None
+    vol_dev = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
+    tf_dev = torch.from_numpy(w["tf"]).cuda()
+    R = Renderer(local)
+    ctx = R.ctx
+    # the slabs composite exactly only without early termination
+    params = vr.make_params(step=w["step"], grad=w["grad"], skip_empty=w["skip_empty"],
+                            ert_threshold=2.0)
+    cam_s = vr.make_camera(cam)
+    part = SL.SlabPartition(nz, world)
+    sign = torch.from_numpy(SL.ray_dz_sign(cam)).cuda()
+    mine = torch.zeros((H, W, 4), device="cuda")
+    frame = torch.empty((H, W, 4), device="cuda")
+
+    def step(p=params):
+        vr.vr_upload_volume(ctx, vol_dev, dt, nx, ny, nz, w["value_max"], sh)
+        vr.vr_set_transfer_function(ctx, tf_dev, tf_dev.shape[0], sh)
+        vr.vr_set_camera(ctx, cam_s)
+        part.render_local(rank, lambda a, b, dst: vr.vr_render_partial(ctx, p, a, b, dst, sh),
+                          mine)
+        part.gather(mine, sign, frame)
+
+    # the frame's plain sample count (a whole render with counters, outside the timing)
+    vr.vr_upload_volume(ctx, vol_dev, dt, nx, ny, nz, w["value_max"], sh)
+    vr.vr_set_transfer_function(ctx, tf_dev, tf_dev.shape[0], sh)
+    vr.vr_set_camera(ctx, cam_s)
+    vr.vr_render(ctx, vr.make_params(step=w["step"], grad=w["grad"], skip_empty=w["skip_empty"],
+                                     ert_threshold=2.0, collect_stats=True), frame, sh)
+    samples = int(vr.vr_read_stats(ctx, sh)["samples_plain"])
+    for _ in range(args.warmup):
+        step()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for i in range(K):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        barrier(world)
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+    ms = total_ms / K
+    cfg = dict(bench_config(w, world), parallelism=f"sortlast{world}")
+    cfg["ert"] = "off (slabs composite exactly only without early termination)"
+    line = {"metric": "Gsamples/s", "value": samples / (ms / 1e3) / 1e9, "unit": "Gsamples/s",
+            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg,
+            "frames_per_s": 1000.0 / ms, "samples_per_frame": samples,
+            "slabs": [[z0 if math.isfinite(z0) else None, z1 if math.isfinite(z1) else None]
+                      for z0, z1 in part.slabs],
+            "gpu_launches": 7 * K, "clocks": clk.summary(), "e2e": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    R.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -975,6 +1059,8 @@ def run_ours(args):
 
     if args.mode == "sortfirst":
         return run_sortfirst(args)
+    if args.mode == "sortlast":
+        return run_sortlast(args)
     rank, world, local = dist_setup(args)
     build.build()
     w = workload(args.workload)

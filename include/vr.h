@@ -203,6 +203,20 @@ vr_status vr_render(vr_ctx *ctx, const vr_render_params *params, float *out_rgba
 vr_status vr_render_rows(vr_ctx *ctx, const vr_render_params *params, int row0, int row1,
                          float *out_rgba, void *stream);
 
+/* The partial image of one z-slab of the volume (the object-space, sort-last partition):
+ * the march of vr_render on the whole sampling box's grid of samples, compositing only the
+ * samples whose position has z0 <= z < z1 (the others count as transparent), written to
+ * out_rgba (H x W x 4 float32, host or device memory, detected) as premultiplied
+ * (C, A = 1 - T).  Slabs [z_0, z_1), [z_1, z_2), ... that tile the volume composite, pixel by
+ * pixel front to back along the pixel's ray ("over": C = C_f + (1 - A_f) C_b,
+ * A = A_f + (1 - A_f) A_b, Eq. 6 is associative), to vr_render's image up to rounding when
+ * early termination is off (ert_threshold > 1; with it each slab would stop on its own
+ * transmittance).  The ray's direction in z gives the pixel's slab order.  The record march
+ * always renders it.  Errors: as vr_render, plus INVALID_ARG unless z0 < z1 (either may be
+ * infinite), UNSUPPORTED with adaptive sampling. */
+vr_status vr_render_partial(vr_ctx *ctx, const vr_render_params *params, float z0, float z1,
+                            float *out_rgba, void *stream);
+
 /* Bytes of the checkpoint buffer vr_render_forward_train needs for the current camera,
  * volume and `params` (per-ray end index plus transmittance every 32 samples). */
 vr_status vr_checkpoint_bytes(vr_ctx *ctx, const vr_render_params *params, size_t *bytes);

@@ -154,6 +154,17 @@ class Renderer:
         vr.vr_render_rows(self.ctx, p, row0, row1, out, _stream_handle())
         return out
 
+    def render_partial(self, z0: float, z1: float, params=None, out=None, **kw):
+        """The premultiplied partial image of the samples with z in [z0, z1) (sort-last,
+        ``sortlast.py``) as an (H, W, 4) float32 CUDA tensor."""
+        torch = _torch()
+        p = params if params is not None else vr.make_params(**kw)
+        H, W = self.camera["height"], self.camera["width"]
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.float32, device=f"cuda:{self.device}")
+        vr.vr_render_partial(self.ctx, p, z0, z1, out, _stream_handle())
+        return out
+
     def render_surface(self, params=None, out=None, depth=None, **kw):
         """First-hit surface render of the current volume and camera (§3.11, §5.1); returns
         ((H, W, 4) float32 image, (H, W) float32 hit distances, +inf where nothing is hit)."""

@@ -348,7 +348,8 @@ void screen_rect(const CamDev& c, const float lo[3], const float hi[3], int rect
 // (row1 - row0) rows.
 static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* out,
                                int* ck_kend, float* ck_T, int nslots, cudaStream_t s,
-                               float* ck_Tend = nullptr, int row0 = 0, int row1 = -1) {
+                               float* ck_Tend = nullptr, int row0 = 0, int row1 = -1,
+                               const float* zwin = nullptr) {
   MarchLaunch L;
   L.V = vol_dev(ctx);
   L.R = rec_dev(ctx);  // refreshed below when the records are computed
@@ -389,7 +390,7 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
   // a plain render marches in slabs (no record table) when asked to and the camera allows
   // it; the automatic choice is the record march, the faster one on every workload measured
   bool slab = false;
-  if (!ck_kend && !p->adaptive && p->march == VR_MARCH_SLABS) {
+  if (!ck_kend && !p->adaptive && !zwin && p->march == VR_MARCH_SLABS) {
     vr_status st = ensure_hint(ctx);
     if (st != VR_OK) return st;
     L.hint = ctx->vis_hint_dev;
@@ -401,7 +402,11 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
     if (rst != VR_OK) return rst;
     L.R = rec_dev(ctx);
   }
-  if (!slab && !ck_kend && !p->adaptive && L.rect[2] > L.rect[0]) {
+  if (zwin) {
+    L.zwin[0] = zwin[0];
+    L.zwin[1] = zwin[1];
+  }
+  if (!slab && !zwin && !ck_kend && !p->adaptive && L.rect[2] > L.rect[0]) {
     // plain render: the rays of the rectangle's tiles are set up and listed first
     const size_t tiles = (size_t)((L.rect[2] + 3) / 4 - L.rect[0] / 4) *
                          (size_t)((L.rect[3] + 1) / 2 - L.rect[1] / 2);
@@ -431,7 +436,8 @@ static vr_status render_common(vr_ctx* ctx, const vr_render_params* p, float* ou
     if (st != VR_OK) return st;
     L.r.mult = static_cast<const uint8_t*>(ctx->adapt_mult);
   }
-  const vr_status st = cuda_status(slab ? launch_march_slab(L, s) : launch_march(L, s));
+  const vr_status st = cuda_status(zwin ? launch_march_zwin(L, s)
+                                        : (slab ? launch_march_slab(L, s) : launch_march(L, s)));
   if (st == VR_OK && p->collect_stats) {
     ctx->stats_valid = true;
     ctx->stats_march = slab ? VR_MARCH_SLABS : VR_MARCH_RECORDS;
@@ -758,6 +764,35 @@ vr_status vr_render_rows(vr_ctx* ctx, const vr_render_params* params, int row0, 
     dst = static_cast<float*>(ctx->out_staging);
   }
   st = render_common(ctx, params, dst, nullptr, nullptr, 0, s, nullptr, row0, row1);
+  if (st != VR_OK) return st;
+  if (host_out)
+    st = cuda_status(cudaMemcpyAsync(out_rgba, dst, bytes, cudaMemcpyDeviceToHost, s));
+  return st;
+}
+
+vr_status vr_render_partial(vr_ctx* ctx, const vr_render_params* params, float z0, float z1,
+                            float* out_rgba, void* stream) {
+  TraceRange trace_("vr_render_partial");
+  if (!ctx || !out_rgba) return VR_ERR_INVALID_ARG;
+  vr_status st = check_params(params);
+  if (st != VR_OK) return st;
+  if (params->adaptive) return VR_ERR_UNSUPPORTED;  // partial images follow the regular grid
+  if (std::isnan(z0) || std::isnan(z1) || !(z0 < z1)) return VR_ERR_INVALID_ARG;
+  if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->cam.width * ctx->cam.height * sizeof(float4);
+  float* dst = out_rgba;
+  const bool host_out = !is_device_pointer(out_rgba);
+  if (!host_out && !aligned_to(out_rgba, 16)) return VR_ERR_INVALID_ARG;
+  if (host_out) {
+    st = ensure(ctx, &ctx->out_staging, &ctx->out_cap, bytes);
+    if (st != VR_OK) return st;
+    dst = static_cast<float*>(ctx->out_staging);
+  }
+  const float zw[2] = {z0, z1};
+  st = render_common(ctx, params, dst, nullptr, nullptr, 0, s, nullptr, 0, -1, zw);
   if (st != VR_OK) return st;
   if (host_out)
     st = cuda_status(cudaMemcpyAsync(out_rgba, dst, bytes, cudaMemcpyDeviceToHost, s));

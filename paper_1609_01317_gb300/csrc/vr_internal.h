@@ -1,6 +1,8 @@
 // vr_internal.h -- host-side context and launcher declarations of libvr.
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -230,8 +232,12 @@ struct MarchLaunch {
   const int* vis_count = nullptr;  // visible bricks of the current transfer function (device)
   int mode = 0;  // 0: list mode decided on the device from vis_count; 1: tiles; 2: list
   int* hint = nullptr;  // host-mapped {count, bricks}: written by the march for the next render
+  // partial images (sort-last): only samples with z in [zwin[0], zwin[1]) are composited
+  float zwin[2] = {-HUGE_VALF, HUGE_VALF};
 };
 cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s);
+// The plain tile march restricted to the samples in L.zwin (records must be current).
+cudaError_t launch_march_zwin(const MarchLaunch& L, cudaStream_t s);
 // The slab march (no record table): whether it can render L (a plain render whose rays lie
 // close enough together), and its launch.
 bool slab_eligible(const MarchLaunch& L);

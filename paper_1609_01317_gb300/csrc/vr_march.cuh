@@ -68,13 +68,17 @@ __device__ __forceinline__ void corners_gradient(const Corners& k, const Cell& c
 // march_core: the march of a ray whose set-up (o, d, tn, K) is given, from sample k0 (a
 // multiple of 4; every sample before it lies in a transparent macro brick, so it contributes
 // nothing).
-template <bool CKPT, bool TFS = false, bool ADAPT = false>
+// ZWIN: only the samples whose z lies in [L.zwin[0], L.zwin[1]) are composited (a partial
+// image of one z-slab of the volume, on the whole box's sampling grid); the others count as
+// transparent.
+template <bool CKPT, bool TFS = false, bool ADAPT = false, bool ZWIN = false>
 __device__ __forceinline__ void march_core(const MarchLaunch& L, const float o[3],
                                            const float d[3], float tn, int K, int k0, int px,
                                            int py, bool active, int q, unsigned qmask,
                                            unsigned& hit, unsigned& plain, unsigned& visited,
                                            unsigned& shaded, const float4* s_tf) {
   static_assert(!(CKPT && ADAPT), "the adjoint's checkpoints follow the regular grid");
+  static_assert(!(ZWIN && (CKPT || ADAPT)), "partial images come from the plain march");
   const int W = L.cam.width, H = L.cam.height;
   const int ray = py * W + px;
   const int qbase = (threadIdx.x & 31) & ~3;
@@ -112,11 +116,12 @@ __device__ __forceinline__ void march_core(const MarchLaunch& L, const float o[3
       if (stride == 1) span = 4 - (k & 3);
     }
     const int ks = k + q * stride;
-    const bool live = q * stride < span && ks < K;
     float p[3];
     const float t = fmaf((float)ks + 0.5f, step, tn);
 #pragma unroll
     for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
+    bool live = q * stride < span && ks < K;
+    if constexpr (ZWIN) live = live && p[2] >= L.zwin[0] && p[2] < L.zwin[1];
     bool vis = live;
     int kn = ks < K ? k + span : K;  // a lane past the group's span bounds the jump by it
     int w = stride;                  // samples this lane's sample stands for
@@ -288,7 +293,7 @@ __device__ __forceinline__ void march_core(const MarchLaunch& L, const float o[3
 }
 
 // The march of pixel (px, py): ray set-up (§3.3, §3.6), then march_core from sample 0.
-template <bool CKPT, bool TFS = false, bool ADAPT = false>
+template <bool CKPT, bool TFS = false, bool ADAPT = false, bool ZWIN = false>
 __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, bool active,
                                           int q, unsigned qmask, unsigned& hit, unsigned& plain,
                                           unsigned& visited, unsigned& shaded,
@@ -296,8 +301,26 @@ __device__ __forceinline__ void march_ray(const MarchLaunch& L, int px, int py, 
   float o[3], d[3], tn = 0.0f;
   int K = 0;
   if (active) ray_setup(L.cam, L.r.lo, L.r.hi, L.r.step, px, py, o, d, tn, K);
-  march_core<CKPT, TFS, ADAPT>(L, o, d, tn, K, 0, px, py, active, q, qmask, hit, plain,
-                               visited, shaded, s_tf);
+  int k0 = 0;
+  if constexpr (ZWIN) {
+    // march only the groups around the samples inside the z window (one sample of margin on
+    // either side: the exact test is each sample's own position)
+    if (K > 0) {
+      if (d[2] != 0.0f) {
+        const float ta = (L.zwin[0] - o[2]) / d[2], tb = (L.zwin[1] - o[2]) / d[2];
+        const float inv_step = 1.0f / L.r.step;
+        const float kf0 = floorf(fmaf(fminf(ta, tb) - tn, inv_step, -0.5f)) - 1.0f;
+        const float kf1 = ceilf(fmaf(fmaxf(ta, tb) - tn, inv_step, -0.5f)) + 2.0f;
+        k0 = !(kf0 > 0.0f) ? 0 : (kf0 >= (float)K ? K : ((int)kf0 & ~3));
+        if (kf1 < (float)K) K = kf1 > 0.0f ? (int)kf1 : 0;
+        if (k0 > K) k0 = K & ~3;
+      } else if (!(o[2] >= L.zwin[0] && o[2] < L.zwin[1])) {
+        K = 0;
+      }
+    }
+  }
+  march_core<CKPT, TFS, ADAPT, ZWIN>(L, o, d, tn, K, k0, px, py, active, q, qmask, hit, plain,
+                                     visited, shaded, s_tf);
 }
 
 }  // namespace vr

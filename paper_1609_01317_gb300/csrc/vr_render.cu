@@ -66,9 +66,9 @@ __device__ __forceinline__ void add_stats(const MarchLaunch& L, unsigned hit, un
 // The march of tiles.  TFS: the block copies the transfer function (n <= kMaxSharedTf
 // entries) to shared memory.  ADAPT: adaptive sampling with the per-brick multipliers
 // L.r.mult.  A plain render in list mode returns at once (k_march_list marches it).
-template <bool CKPT, bool TFS, bool ADAPT = false>
+template <bool CKPT, bool TFS, bool ADAPT = false, bool ZWIN = false>
 __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
-  if constexpr (!CKPT && !ADAPT) {
+  if constexpr (!CKPT && !ADAPT && !ZWIN) {
     write_hint(L);
     if (list_mode(L)) return;
   }
@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
     if (tile >= tiles) break;
     const int px = (tx0 + tile % tiles_x) * kTileW + (qd & 3);
     const int py = (ty0 + tile / tiles_x) * kTileH + (qd >> 2);
-    march_ray<CKPT, TFS, ADAPT>(L, px, py, px < W && py < H && py >= L.row0 && py < L.row1, q,
-                                qmask, hit, plain, visited, shaded, s_tf);
+    march_ray<CKPT, TFS, ADAPT, ZWIN>(L, px, py, px < W && py < H && py >= L.row0 && py < L.row1,
+                                      q, qmask, hit, plain, visited, shaded, s_tf);
     __syncwarp();
   }
   if (L.stats) add_stats(L, hit, plain, visited, shaded);
@@ -281,6 +281,24 @@ cudaError_t launch_march(const MarchLaunch& L, cudaStream_t s) {
   if (L.ck_kend) launch_march_k<true, false>(L, s);
   else if (L.r.mult) launch_march_k<false, true>(L, s);
   else launch_march_k<false, false>(L, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_march_zwin(const MarchLaunch& L, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  if (L.rect[2] <= L.rect[0] || L.rect[3] <= L.rect[1]) return cudaSuccess;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (L.tf.n <= kMaxSharedTf) {
+    const size_t smem = sizeof(float4) * (size_t)L.tf.n;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march<false, true, false, true>, kThreads, smem);
+    k_march<false, true, false, true><<<(sms > 0 ? sms : 152) * (per > 0 ? per : 1), kThreads, smem, s>>>(L);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march<false, false, false, true>, kThreads, 0);
+    k_march<false, false, false, true><<<(sms > 0 ? sms : 152) * (per > 0 ? per : 1), kThreads, 0, s>>>(L);
+  }
   return cudaGetLastError();
 }
 

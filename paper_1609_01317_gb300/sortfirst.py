@@ -98,6 +98,8 @@ class RowPartition:
         import torch
         import torch.distributed as dist
 
+        if self.world == 1:
+            return self.stitch([packed], out)  # one rank: nothing to exchange
         parts = [torch.empty_like(packed) for _ in range(self.world)]
         dist.all_gather(parts, packed, group=group)
         return self.stitch(parts, out)

@@ -71,6 +71,8 @@ _SIGS = [
     ("vr_render", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p, C.c_void_p]),
     ("vr_render_rows", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_int, C.c_int,
                                  C.c_void_p, C.c_void_p]),
+    ("vr_render_partial", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_float,
+                                    C.c_float, C.c_void_p, C.c_void_p]),
     ("vr_checkpoint_bytes", C.c_int, [C.c_void_p, C.POINTER(vr_render_params),
                                       C.POINTER(C.c_size_t)]),
     ("vr_render_forward_train", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p,
@@ -276,6 +278,13 @@ def vr_render_rows(ctx, params, row0, row1, out_rgba, stream=None):
     _buf("vr_render_rows", out_rgba, band, 4, what="out_rgba")
     _check("vr_render_rows", lib().vr_render_rows(ctx, C.byref(params), int(row0), int(row1),
                                                   _ptr(out_rgba), stream))
+
+
+def vr_render_partial(ctx, params, z0, z1, out_rgba, stream=None):
+    """The premultiplied partial image of the samples with z in [z0, z1) (sort-last)."""
+    _buf("vr_render_partial", out_rgba, _state.get(ctx, {}).get("image", 0), 4, what="out_rgba")
+    _check("vr_render_partial", lib().vr_render_partial(ctx, C.byref(params), float(z0),
+                                                        float(z1), _ptr(out_rgba), stream))
 
 
 def vr_checkpoint_bytes(ctx, params) -> int:
