@@ -1,7 +1,9 @@
-"""Run every renderer over volumes and views chosen to reach the edges of their buffers, in
+"""Run every renderer (the tile and slab marches, row bands, z-window partial images and the
+multi-view adjoint included) over volumes and views chosen to reach the edges of their buffers, in
 the library named by VR_LIBRARY (the bounds-checked build), and print one JSON line with the
 out-of-range index count of every context.  Run as a child process by test_gpu_bounds.py."""
 import json
+import math
 import os
 import sys
 
@@ -45,6 +47,7 @@ def main():
             try:
                 r.upload_volume(vol, vmax)
                 r.set_transfer_function(P.tf_random(91, 48, alpha_max=0.6))
+                cks = []
                 for cam in views(shp):
                     r.set_camera(cam)
                     H, W = cam["height"], cam["width"]
@@ -53,8 +56,15 @@ def main():
                                    dict(clip_lo=(0.5, 0.25, 0.0), clip_hi=(6.5, 5.0, 3.75)),
                                    dict(adapt_range=(vmax, vmax * 0.1))):
                             r.render(params=vr.make_params(grad=grad, **kw))
+                        r.render(params=vr.make_params(grad=grad, march="slabs"))
                         r.render_surface(params=vr.make_surface_params(
                             step=0.75, iso_lo=0.3 * vmax, iso_hi=3.0e38, refine=5, grad=grad))
+                    r.render_rows(H // 3, H - H // 4, params=vr.make_params())
+                    nz = float(shp[2])
+                    for z0, z1 in ((-math.inf, 0.5 * nz), (0.5 * nz, math.inf),
+                                   (nz + 4.0, math.inf), (-math.inf, -2.0), (0.25, 0.3)):
+                        r.render_partial(z0, z1, params=vr.make_params(grad="zucker_hummel",
+                                                                       ert_threshold=2.0))
                     p = vr.make_params(grad="sobel3d", ert_threshold=0.9)
                     nb = vr.vr_checkpoint_bytes(r.ctx, p)
                     ck = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
@@ -65,6 +75,13 @@ def main():
                     gt = torch.zeros((48, 4), dtype=torch.float32, device="cuda")
                     gi = torch.ones((H, W, 4), device="cuda")
                     vr.vr_render_backward(r.ctx, p, ck[off:off + nb], gi, gv, gt)
+                    cks.append((cam, ck, ck[off:off + nb], gi))
+                # every view's adjoint in one launch
+                p = vr.make_params(grad="sobel3d", ert_threshold=0.9)
+                gv = torch.zeros(vol.shape, dtype=torch.float32, device="cuda")
+                gt = torch.zeros((48, 4), dtype=torch.float32, device="cuda")
+                vr.vr_render_backward_views(r.ctx, p, [c[0] for c in cks], [c[2] for c in cks],
+                                            [c[3] for c in cks], gv, gt)
                 top = np.array(shp, np.float64) - 1.0
                 corners = np.array([[(k & 1) * top[0], (k >> 1 & 1) * top[1], (k >> 2 & 1) * top[2]]
                                     for k in range(8)])
