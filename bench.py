@@ -1268,17 +1268,22 @@ def run_ours(args):
             done[0].synchronize()
             checks += float(host_out[0][probe][3])
         serial_s = (time.perf_counter() - t0) / ke
-        t0 = time.perf_counter()
-        for i in range(ke):
-            j = i % DEPTH
-            if i >= DEPTH:
-                done[j].synchronize()  # step i - DEPTH finished: read its image
+        # the pipelined loop is driven from one host thread, so host scheduling shows in it:
+        # three runs of ke steps each, the median reported and all three listed
+        e2e_runs = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            for i in range(ke):
+                j = i % DEPTH
+                if i >= DEPTH:
+                    done[j].synchronize()  # step i - DEPTH finished: read its image
+                    checks += float(host_out[j][probe][3])
+                e2e_step(j)
+            for j in range(DEPTH):
+                done[j].synchronize()
                 checks += float(host_out[j][probe][3])
-            e2e_step(j)
-        for j in range(DEPTH):
-            done[j].synchronize()
-            checks += float(host_out[j][probe][3])
-        e2e_s = (time.perf_counter() - t0) / ke
+            e2e_runs.append((time.perf_counter() - t0) / ke)
+        e2e_s = statistics.median(e2e_runs)
         ok = ok and torch.equal(host_out[(ke - 1) % DEPTH], ref_out)
         # the host link's own rates (plain copies of the same bytes): the bound of any step
         # that moves the volume in and the image out
@@ -1316,8 +1321,10 @@ def run_ours(args):
         line["e2e"] = {"value": samples / e2e_s / 1e9, "unit": "Gsamples/s",
                        "h2d_bytes_per_step": int(vol.nbytes + w["tf"].nbytes),
                        "d2h_bytes_per_step": int(H * W * 16), "ms_per_step": e2e_s * 1e3,
+                       "runs_ms": [round(r * 1e3, 4) for r in e2e_runs],
                        "pipeline": f"{DEPTH} contexts on {DEPTH} streams (a step's copies overlap "
-                                   "the previous steps' kernels); host reads every step's image",
+                                   "the previous steps' kernels); host reads every step's image; "
+                                   "median of 3 runs",
                        "serial_ms_per_step": serial_s * 1e3,
                        "serial_value": samples / serial_s / 1e9,
                        "steps": ke, "matches_device_result": bool(ok),

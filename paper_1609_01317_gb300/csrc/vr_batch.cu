@@ -29,7 +29,7 @@ struct BatchLaunch {
 };
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_march_batch(const BatchLaunch B) {
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_march_batch(const BatchLaunch B) {
   const int lane = threadIdx.x & 31;
   const int q = lane & 3, qd = lane >> 2;
   const unsigned qmask = 0xFu << (lane & ~3);

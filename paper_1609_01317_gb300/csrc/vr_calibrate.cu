@@ -72,10 +72,8 @@ __device__ __forceinline__ float gather_core(const RecDev& R, const float p[3], 
   const Cell c = table_cell(p, n);
   Corners cr;
   corners_load(R, c, cr);
-  const float s = corners_value(cr, c);
-  float g[3];
-  corners_gradient(cr, c, g);
-  return s + g[0] + g[1] + g[2];
+  const float4 bl = corners_blend(cr, c);
+  return bl.w + bl.x + bl.y + bl.z;
 }
 
 // Warp task: 8 rays (4 x 2 pixels) x 64 samples, four lanes per ray on consecutive samples.

@@ -10,44 +10,73 @@
 
 namespace vr {
 
-// Corner records of cell c and the trilinear value (raw units), lerps along x, y, z.
+// brick_of and cell_of of the device header, from ip = floor(p) computed once per sample
+// (the brick test and the cell share it).
+__device__ __forceinline__ int brick_of_floor(const VolDev& V, const int ip[3], int b[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int i = ip[a] >> kBrickShift;
+    b[a] = i < 0 ? 0 : (i >= V.nb[a] ? V.nb[a] - 1 : i);
+  }
+  return b[0] + V.nb[0] * (b[1] + V.nb[1] * b[2]);
+}
+
+__device__ __forceinline__ Cell cell_of_floor(const VolDev& V, const float p[3], const int ip[3]) {
+  Cell c;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int top = V.n[a] > 1 ? V.n[a] - 2 : 0;
+    const int i = ip[a] < 0 ? 0 : (ip[a] > top ? top : ip[a]);
+    c.ib[a] = i;
+    c.f[a] = p[a] - (float)i;
+  }
+  c.base = (c.ib[0] + kPadLo) + V.px * (c.ib[1] + kPadLo) + V.pxy * (c.ib[2] + kPadLo);
+  return c;
+}
+
+// The 8 corner records of a cell.
 struct Corners {
   float4 r[8];  // index bit 0: +x, bit 1: +y, bit 2: +z
 };
 
+// Record indices fit in 32 bits: the upload refuses volumes of 2^31 voxels or more.
 __device__ __forceinline__ void corners_load(const RecDev& R, const Cell& c, Corners& k) {
-  const size_t base = (size_t)VR_CHECK(
-      R.bounds, (size_t)c.ib[0] + (size_t)R.n[0] * ((size_t)c.ib[1] + (size_t)R.n[1] * c.ib[2]), 0,
+  const int base = (int)VR_CHECK(
+      R.bounds, c.ib[0] + R.n[0] * (c.ib[1] + R.n[1] * c.ib[2]), 0,
       (long long)R.n[0] * R.n[1] * R.n[2] - 1 - corner_span(R));
-  const float4* __restrict__ p = R.rec + base;
+  const float4* __restrict__ p = R.rec;
 #pragma unroll
   for (int i = 0; i < 8; ++i)
-    k.r[i] = __ldg(p + ((i & 1) ? R.sx : 0) + ((i & 2) ? R.sy : 0) + ((i & 4) ? R.sz : 0));
+    k.r[i] = __ldg(p + (base + ((i & 1) ? R.sx : 0) + ((i & 2) ? R.sy : 0) + ((i & 4) ? R.sz : 0)));
 }
 
-__device__ __forceinline__ float corners_value(const Corners& k, const Cell& c) {
-  const float x00 = lerpf(k.r[0].w, k.r[1].w, c.f[0]), x10 = lerpf(k.r[2].w, k.r[3].w, c.f[0]);
-  const float x01 = lerpf(k.r[4].w, k.r[5].w, c.f[0]), x11 = lerpf(k.r[6].w, k.r[7].w, c.f[0]);
-  const float y0 = lerpf(x00, x10, c.f[1]), y1 = lerpf(x01, x11, c.f[1]);
-  return lerpf(y0, y1, c.f[2]);
+// lerpf on two channels at once: one packed FP32 subtraction and one packed fused
+// multiply-add (sm_100 and later), each channel rounded exactly as lerpf rounds it.
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 f) {
+  return __ffma2_rn(f, __fadd2_rn(b, make_float2(-a.x, -a.y)), a);
 }
 
-// Trilinear blend of the corner gradients (unscaled operator gradient at the sample).
-__device__ __forceinline__ void corners_gradient(const Corners& k, const Cell& c, float g[3]) {
-  const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
-  const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
-  const float w[8] = {gx * gy * gz, fx * gy * gz, gx * fy * gz, fx * fy * gz,
-                      gx * gy * fz, fx * gy * fz, gx * fy * fz, fx * fy * fz};
-  float a = 0.f, b = 0.f, d = 0.f;
+// Trilinear interpolation (§3.4) of all four channels of the corner records at the sample:
+// (G_x, G_y, G_z, V), lerps along x, then y, then z, two channels per packed instruction.
+// The value channel takes the same seven lerps, in the same order, as the adjoint's
+// recomputation of the forward (record_value), so both see the same opacities bit for bit.
+// The gradient is blended before the transfer function says whether the sample is shaded:
+// that frees the 32 registers of the corners early and lets the march run 8 blocks of 128
+// threads per SM (measured faster than blending only shaded samples at 7 blocks).
+__device__ __forceinline__ float4 corners_blend(const Corners& k, const Cell& c) {
+  const float2 fx = make_float2(c.f[0], c.f[0]), fy = make_float2(c.f[1], c.f[1]),
+               fz = make_float2(c.f[2], c.f[2]);
+  float2 lo[4], hi[4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    a = fmaf(w[i], k.r[i].x, a);
-    b = fmaf(w[i], k.r[i].y, b);
-    d = fmaf(w[i], k.r[i].z, d);
+  for (int i = 0; i < 4; ++i) {
+    const float4 a = k.r[2 * i], b = k.r[2 * i + 1];
+    lo[i] = lerp2(make_float2(a.x, a.y), make_float2(b.x, b.y), fx);
+    hi[i] = lerp2(make_float2(a.z, a.w), make_float2(b.z, b.w), fx);
   }
-  g[0] = a;
-  g[1] = b;
-  g[2] = d;
+  const float2 l0 = lerp2(lo[0], lo[1], fy), h0 = lerp2(hi[0], hi[1], fy);
+  const float2 l1 = lerp2(lo[2], lo[3], fy), h1 = lerp2(hi[2], hi[3], fy);
+  const float2 l = lerp2(l0, l1, fz), h = lerp2(h0, h1, fz);
+  return make_float4(l.x, l.y, h.x, h.y);
 }
 
 // March one ray with a quad: lane q evaluates sample k + q of every group of four
@@ -71,7 +100,14 @@ __device__ __forceinline__ void corners_gradient(const Corners& k, const Cell& c
 // ZWIN: only the samples whose z lies in [L.zwin[0], L.zwin[1]) are composited (a partial
 // image of one z-slab of the volume, on the whole box's sampling grid); the others count as
 // transparent.
-template <bool CKPT, bool TFS = false, bool ADAPT = false, bool ZWIN = false>
+// JLOOP: a quad's run of consecutive jumps is taken in an inner loop of its own, so that a
+// quad crossing empty space holds the other quads of its warp for its jumps only, not for a
+// whole march iteration per jump; without it every jump ends the iteration.  The sequence of
+// groups, and so the image, is the same either way.  The inner loop ends: every jump moves k
+// on by at least 4 samples or to K (the progress rule of the jump, below).  Measured on GB300:
+// faster for the tile march on the dense CT frame, slower for the list march on sparse data
+// and for adaptive sampling (off for both).
+template <bool CKPT, bool TFS = false, bool ADAPT = false, bool ZWIN = false, bool JLOOP = !ADAPT>
 __device__ __forceinline__ void march_core(const MarchLaunch& L, const float o[3],
                                            const float d[3], float tn, int K, int k0, int px,
                                            int py, bool active, int q, unsigned qmask,
@@ -90,108 +126,125 @@ __device__ __forceinline__ void march_core(const MarchLaunch& L, const float o[3
 #pragma unroll
   for (int a = 0; a < 3; ++a) inv_d[a] = d[a] != 0.0f ? 1.0f / d[a] : 0.0f;
   while (k < K) {
-    int stride = 1, span = 4;  // samples between the quad's lanes; samples the group covers
-    if constexpr (ADAPT) {
-      float p0[3];
-      const float t0 = fmaf((float)k + 0.5f, step, tn);
+    int stride, span, ks, kn, w;  // samples between the quad's lanes; samples the group covers
+    float p[3];
+    int ip[3];
+    bool live, vis;
+    bool jumped = false;  // without JLOOP: this iteration's group jumped
+    for (;;) {
+      stride = 1;
+      span = 4;
+      if constexpr (ADAPT) {
+        float p0[3];
+        const float t0 = fmaf((float)k + 0.5f, step, tn);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) p0[a] = fmaf(t0, d[a], o[a]);
-      int b0[3];
-      brick_of(L.V, p0, b0);
-      const int mi0 = macro_of(L.V, b0);
-      const int m0 = __ldg(L.r.mult + VR_CHECK(L.V.bounds, mi0, 0, L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1));
-      if (m0 > 1 && (k & (m0 - 1)) == 0) {
-        const int kl = min(k + 4 * m0 - 1, K - 1);
-        float pl[3];
-        const float tl = fmaf((float)kl + 0.5f, step, tn);
+        for (int a = 0; a < 3; ++a) p0[a] = fmaf(t0, d[a], o[a]);
+        int b0[3];
+        brick_of(L.V, p0, b0);
+        const int mi0 = macro_of(L.V, b0);
+        const int m0 = __ldg(L.r.mult + VR_CHECK(L.V.bounds, mi0, 0, L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1));
+        if (m0 > 1 && (k & (m0 - 1)) == 0) {
+          const int kl = min(k + 4 * m0 - 1, K - 1);
+          float pl[3];
+          const float tl = fmaf((float)kl + 0.5f, step, tn);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) pl[a] = fmaf(tl, d[a], o[a]);
-        int bl[3];
-        brick_of(L.V, pl, bl);
-        if (macro_of(L.V, bl) == mi0) {
-          stride = m0;
-          span = 4 * m0;
+          for (int a = 0; a < 3; ++a) pl[a] = fmaf(tl, d[a], o[a]);
+          int bl[3];
+          brick_of(L.V, pl, bl);
+          if (macro_of(L.V, bl) == mi0) {
+            stride = m0;
+            span = 4 * m0;
+          }
+        }
+        if (stride == 1) span = 4 - (k & 3);
+      }
+      ks = k + q * stride;
+      const float t = fmaf((float)ks + 0.5f, step, tn);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) ip[a] = (int)floorf(p[a]);  // shared by brick and cell
+      live = q * stride < span && ks < K;
+      if constexpr (ZWIN) live = live && p[2] >= L.zwin[0] && p[2] < L.zwin[1];
+      vis = live;
+      kn = ks < K ? k + span : K;  // a lane past the group's span bounds the jump by it
+      w = stride;                  // samples this lane's sample stands for
+      if constexpr (ADAPT) {
+        if (live && stride == 1) {
+          int bm[3];
+          brick_of(L.V, p, bm);
+          w = __ldg(L.r.mult + VR_CHECK(L.V.bounds, macro_of(L.V, bm), 0,
+                                        L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1));
         }
       }
-      if (stride == 1) span = 4 - (k & 3);
-    }
-    const int ks = k + q * stride;
-    float p[3];
-    const float t = fmaf((float)ks + 0.5f, step, tn);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) p[a] = fmaf(t, d[a], o[a]);
-    bool live = q * stride < span && ks < K;
-    if constexpr (ZWIN) live = live && p[2] >= L.zwin[0] && p[2] < L.zwin[1];
-    bool vis = live;
-    int kn = ks < K ? k + span : K;  // a lane past the group's span bounds the jump by it
-    int w = stride;                  // samples this lane's sample stands for
-    if constexpr (ADAPT) {
-      if (live && stride == 1) {
-        int bm[3];
-        brick_of(L.V, p, bm);
-        w = __ldg(L.r.mult + VR_CHECK(L.V.bounds, macro_of(L.V, bm), 0,
-                                      L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1));
-      }
-    }
-    if (L.r.skip && live) {
-      int b[3];
-      const int bi = brick_of(L.V, p, b);
-      if (!__ldg(L.V.vis + VR_CHECK(L.V.bounds, bi, 0, L.V.nb[0] * L.V.nb[1] * L.V.nb[2] - 1))) {
-        // transparent brick: leave it, or its whole macro brick when that is transparent too
-        vis = false;
-        int shift = kBrickShift;
-        if (L.V.mvis) {
-          const int m[3] = {b[0] >> kMacroShift, b[1] >> kMacroShift, b[2] >> kMacroShift};
-          if (!__ldg(L.V.mvis + VR_CHECK(L.V.bounds, m[0] + L.V.nm[0] * (m[1] + L.V.nm[1] * m[2]),
-                                         0, L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1))) {
-            b[0] = m[0];
-            b[1] = m[1];
-            b[2] = m[2];
-            shift = kBrickShift + kMacroShift;
-            if (L.V.svis) {
-              const int u[3] = {m[0] >> kSuperShift, m[1] >> kSuperShift, m[2] >> kSuperShift};
-              if (!__ldg(L.V.svis + VR_CHECK(L.V.bounds, u[0] + L.V.ns[0] * (u[1] + L.V.ns[1] * u[2]),
-                                             0, L.V.ns[0] * L.V.ns[1] * L.V.ns[2] - 1))) {
-                b[0] = u[0];
-                b[1] = u[1];
-                b[2] = u[2];
-                shift = kBrickShift + kMacroShift + kSuperShift;
+      if (L.r.skip && live) {
+        int b[3];
+        const int bi = brick_of_floor(L.V, ip, b);
+        if (!__ldg(L.V.vis + VR_CHECK(L.V.bounds, bi, 0, L.V.nb[0] * L.V.nb[1] * L.V.nb[2] - 1))) {
+          // transparent brick: leave it, or its whole macro brick when that is transparent too
+          vis = false;
+          int shift = kBrickShift;
+          if (L.V.mvis) {
+            const int m[3] = {b[0] >> kMacroShift, b[1] >> kMacroShift, b[2] >> kMacroShift};
+            if (!__ldg(L.V.mvis + VR_CHECK(L.V.bounds, m[0] + L.V.nm[0] * (m[1] + L.V.nm[1] * m[2]),
+                                           0, L.V.nm[0] * L.V.nm[1] * L.V.nm[2] - 1))) {
+              b[0] = m[0];
+              b[1] = m[1];
+              b[2] = m[2];
+              shift = kBrickShift + kMacroShift;
+              if (L.V.svis) {
+                const int u[3] = {m[0] >> kSuperShift, m[1] >> kSuperShift, m[2] >> kSuperShift};
+                if (!__ldg(L.V.svis + VR_CHECK(L.V.bounds, u[0] + L.V.ns[0] * (u[1] + L.V.ns[1] * u[2]),
+                                               0, L.V.ns[0] * L.V.ns[1] * L.V.ns[2] - 1))) {
+                  b[0] = u[0];
+                  b[1] = u[1];
+                  b[2] = u[2];
+                  shift = kBrickShift + kMacroShift + kSuperShift;
+                }
               }
             }
           }
+          kn = region_exit_sample(b, shift, o, d, inv_d, tn, inv_step);
+          if (kn <= ks) kn = ks + 1;
         }
-        kn = region_exit_sample(b, shift, o, d, inv_d, tn, inv_step);
-        if (kn <= ks) kn = ks + 1;
       }
-    }
-    // a live lane in a visible brick keeps the group; otherwise the group jumps
-    if (((__ballot_sync(qmask, vis) >> qbase) & 0xFu) == 0u) {
-      // the whole group lies in empty bricks: jump
-      kn = max(kn, __shfl_xor_sync(qmask, kn, 1));
-      kn = max(kn, __shfl_xor_sync(qmask, kn, 2));
-      if (CKPT && q == 0) {
-        const int stop = kn < K ? kn : K;
-        for (int j = ((k + kCkptStride - 1) >> 5) << 5; j < stop; j += kCkptStride)
-          if (j > 0) L.ck_T[(size_t)((j >> 5) - 1) * (W * H) + ray] = T;
+      // a live lane in a visible brick keeps the group; otherwise the group jumps
+      if (((__ballot_sync(qmask, vis) >> qbase) & 0xFu) != 0u) break;
+      {
+        // the whole group lies in empty bricks: jump
+        kn = max(kn, __shfl_xor_sync(qmask, kn, 1));
+        kn = max(kn, __shfl_xor_sync(qmask, kn, 2));
+        if (CKPT && q == 0) {
+          const int stop = kn < K ? kn : K;
+          for (int j = ((k + kCkptStride - 1) >> 5) << 5; j < stop; j += kCkptStride)
+            if (j > 0) L.ck_T[(size_t)((j >> 5) - 1) * (W * H) + ray] = T;
+        }
+        // Without adaptive sampling groups stay aligned to multiples of four, so that lane q
+        // always holds the samples k = q (mod 4); the samples of the new group before kn lie
+        // in the bricks just left (transparent: they contribute nothing).  Progress: if every
+        // lane was live, lane 3's exit makes kn >= k + 4, so kn rounded down is still >= k + 4;
+        // otherwise a lane past K set kn = K and the ray ends here (no rounding).
+        k = (ADAPT || kn >= K) ? kn : (kn & ~3);
       }
-      // Without adaptive sampling groups stay aligned to multiples of four, so that lane q
-      // always holds the samples k = q (mod 4); the samples of the new group before kn lie
-      // in the bricks just left (transparent: they contribute nothing).  Progress: if every
-      // lane was live, lane 3's exit makes kn >= k + 4, so kn rounded down is still >= k + 4;
-      // otherwise a lane past K set kn = K and the ray ends here (no rounding).
-      k = (ADAPT || kn >= K) ? kn : (kn & ~3);
-      continue;
+      if (!JLOOP) {
+        jumped = true;
+        break;
+      }
+      if (k >= K) break;
     }
+    if (k >= K) break;
+    if (jumped) continue;
     float alpha = 0.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
     if constexpr (ADAPT) {
       if (stride == 1 && (ks & (w - 1)) != 0) vis = false;  // off its brick's coarser grid
     }
     if (vis) {
       ++visited;
-      const Cell c = cell_of(L.V, p);
+      const Cell c = cell_of_floor(L.V, p, ip);
       Corners cr;
       corners_load(L.R, c, cr);
-      const float s = corners_value(cr, c);
+      const float4 bl = corners_blend(cr, c);
+      const float s = bl.w;
       const TfSample ts = tf_lookup<TFS>(L.tf, s, s_tf);
       alpha = ts.rgba.w;
       if constexpr (ADAPT) {
@@ -202,9 +255,7 @@ __device__ __forceinline__ void march_core(const MarchLaunch& L, const float o[3
       }
       if (alpha != 0.0f) {
         ++shaded;
-        float g[3];
-        corners_gradient(cr, c, g);
-        const float gh[3] = {g[0] * L.r.gscale, g[1] * L.r.gscale, g[2] * L.r.gscale};
+        const float gh[3] = {bl.x * L.r.gscale, bl.y * L.r.gscale, bl.z * L.r.gscale};
         ShadeOut so;
         shade(L.r.sh, L.cam, d, p, gh, ts.rgba, so);
         c0 = so.c[0];

@@ -22,10 +22,10 @@ __global__ void k_probe(const MarchLaunch L, const float* __restrict__ pos, int 
   const Cell c = cell_of(L.V, p);
   Corners cr;
   corners_load(L.R, c, cr);
-  const float s = corners_value(cr, c);
+  const float4 bl = corners_blend(cr, c);
+  const float s = bl.w;
   const TfSample ts = tf_lookup<false>(L.tf, s);
-  float g[3];
-  corners_gradient(cr, c, g);
+  const float g[3] = {bl.x, bl.y, bl.z};
   const float gh[3] = {g[0] * L.r.gscale, g[1] * L.r.gscale, g[2] * L.r.gscale};
   // the direction of the camera ray through p
   float d[3];

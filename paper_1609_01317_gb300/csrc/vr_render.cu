@@ -67,7 +67,7 @@ __device__ __forceinline__ void add_stats(const MarchLaunch& L, unsigned hit, un
 // entries) to shared memory.  ADAPT: adaptive sampling with the per-brick multipliers
 // L.r.mult.  A plain render in list mode returns at once (k_march_list marches it).
 template <bool CKPT, bool TFS, bool ADAPT = false, bool ZWIN = false>
-__global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
+__global__ void __launch_bounds__(kThreads, 8) k_march(const MarchLaunch L) {
   if constexpr (!CKPT && !ADAPT && !ZWIN) {
     write_hint(L);
     if (list_mode(L)) return;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kThreads, 7) k_march(const MarchLaunch L) {
 // persistent, each warp takes the next 8 rays of the list (neighbouring pixels: the list
 // keeps the tiles' order), a quad of lanes per ray, from each ray's first visible group.
 template <bool TFS>
-__global__ void __launch_bounds__(kThreads, 7) k_march_list(const MarchLaunch L) {
+__global__ void __launch_bounds__(kThreads, 8) k_march_list(const MarchLaunch L) {
   write_hint(L);
   if (!list_mode(L)) return;
   extern __shared__ float4 s_tf[];
@@ -137,8 +137,10 @@ __global__ void __launch_bounds__(kThreads, 7) k_march_list(const MarchLaunch L)
       d[0] = b.x; d[1] = b.y; d[2] = b.z; K = __float_as_int(b.w);
       px = c.x; py = c.y; k0 = c.z;
     }
-    march_core<false, TFS, false>(L, o, d, tn, K, k0, px, py, active, q, qmask, hit, plain,
-                                  visited, shaded, s_tf);
+    // no inner jump loop here: on sparse data a quad's runs of jumps are long and uneven, and
+    // the quads that reached a visible group would wait for the longest run (measured slower)
+    march_core<false, TFS, false, false, false>(L, o, d, tn, K, k0, px, py, active, q, qmask,
+                                                hit, plain, visited, shaded, s_tf);
     __syncwarp();
   }
   if (L.stats) add_stats(L, hit, plain, visited, shaded);

@@ -103,13 +103,11 @@ __device__ __forceinline__ void block_min8(int* red, const int v[8]) {
 __device__ __forceinline__ float4 sample_colour(const MarchLaunch& L, const float4* s_tf,
                                                 const Corners& cr, const Cell& c,
                                                 const float p[3], const float d[3]) {
-  const float s = corners_value(cr, c);
-  const TfSample ts = tf_lookup<true>(L.tf, s, s_tf);
+  const float4 bl = corners_blend(cr, c);
+  const TfSample ts = tf_lookup<true>(L.tf, bl.w, s_tf);
   float4 out = make_float4(ts.rgba.w, 0.0f, 0.0f, 0.0f);
   if (ts.rgba.w != 0.0f) {
-    float g[3];
-    corners_gradient(cr, c, g);
-    const float gh[3] = {g[0] * L.r.gscale, g[1] * L.r.gscale, g[2] * L.r.gscale};
+    const float gh[3] = {bl.x * L.r.gscale, bl.y * L.r.gscale, bl.z * L.r.gscale};
     ShadeOut so;
     shade(L.r.sh, L.cam, d, p, gh, ts.rgba, so);
     out.y = so.c[0];
