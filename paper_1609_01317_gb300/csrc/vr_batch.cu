@@ -28,6 +28,8 @@ struct BatchLaunch {
   int tw, th;                // quads per warp tile along x and y (tw * th == 8)
 };
 
+// 1024 threads per SM at every block size, i.e. 64 registers a thread: 32 warps per SM, as the
+// single-frame march (measured faster than the 80 registers the march takes uncapped).
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_march_batch(const BatchLaunch B) {
   const int lane = threadIdx.x & 31;
