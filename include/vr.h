@@ -193,6 +193,17 @@ vr_status vr_set_camera(vr_ctx *ctx, const vr_camera *cam);
  * cleared to (0, 0, 0, 0) first. */
 vr_status vr_render(vr_ctx *ctx, const vr_render_params *params, float *out_rgba, void *stream);
 
+/* vr_render's image with 8 bits per channel, for display and a read-back a quarter the size:
+ * out_rgba8 (H x W x 4 bytes, row-major, host or device memory, detected; device memory
+ * aligned to 4 bytes) receives for every pixel and channel round(255 * clamp(c, 0, 1)) of
+ * the FP32 value c vr_render writes (the premultiplied colour and 1 - T of §3.9, Eq. 6;
+ * product in FP32, round to nearest even) -- bit for bit the quantisation of vr_render's
+ * image.  The FP32 image is rendered into the context's staging buffer and quantised there
+ * by one more kernel.  Host output is copied back on `stream` and is valid once the stream
+ * is synchronised.  Errors: as vr_render. */
+vr_status vr_render_rgba8(vr_ctx *ctx, const vr_render_params *params, unsigned char *out_rgba8,
+                          void *stream);
+
 /* Rows [row0, row1) of the image vr_render would produce for the current volume, transfer
  * function and camera, written to out_rgba as a band of (row1 - row0) x W x 4 float32 (host
  * or device memory, detected), bit for bit equal to those rows of vr_render's image.

@@ -142,6 +142,17 @@ class Renderer:
         vr.vr_render(self.ctx, p, out, _stream_handle())
         return out
 
+    def render_rgba8(self, params=None, out=None, **kw):
+        """``render``'s image with 8 bits per channel (round(255 clamp(c, 0, 1)) of every
+        channel) as an (H, W, 4) uint8 CUDA tensor."""
+        torch = _torch()
+        p = params if params is not None else vr.make_params(**kw)
+        H, W = self.camera["height"], self.camera["width"]
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=f"cuda:{self.device}")
+        vr.vr_render_rgba8(self.ctx, p, out, _stream_handle())
+        return out
+
     def render_rows(self, row0: int, row1: int, params=None, out=None, **kw):
         """Rows [row0, row1) of ``render``'s image as a (row1 - row0, W, 4) float32 CUDA
         tensor (bit for bit those rows of the whole frame)."""

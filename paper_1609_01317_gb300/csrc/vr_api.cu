@@ -6,6 +6,7 @@
 #include <new>
 
 #include "vr_internal.h"
+#include "vr_output.h"
 
 namespace vr {
 
@@ -740,6 +741,34 @@ vr_status vr_render(vr_ctx* ctx, const vr_render_params* params, float* out_rgba
   if (st != VR_OK) return st;
   if (host_out)
     st = cuda_status(cudaMemcpyAsync(out_rgba, dst, bytes, cudaMemcpyDeviceToHost, s));
+  return st;
+}
+
+vr_status vr_render_rgba8(vr_ctx* ctx, const vr_render_params* params, unsigned char* out_rgba8,
+                          void* stream) {
+  TraceRange trace_("vr_render_rgba8");
+  if (!ctx || !out_rgba8) return VR_ERR_INVALID_ARG;
+  vr_status st = check_params(params);
+  if (st != VR_OK) return st;
+  if (!ctx->has_volume || !ctx->has_tf || !ctx->has_camera) return VR_ERR_STATE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_status(cudaGetLastError());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t npix = (size_t)ctx->cam.width * ctx->cam.height;
+  const size_t fbytes = npix * sizeof(float4), bbytes = npix * sizeof(uchar4);
+  const bool host_out = !is_device_pointer(out_rgba8);
+  if (!host_out && !aligned_to(out_rgba8, 4)) return VR_ERR_INVALID_ARG;
+  // the FP32 image goes to the staging buffer, followed (for a host output) by its bytes
+  st = ensure(ctx, &ctx->out_staging, &ctx->out_cap, fbytes + (host_out ? bbytes : 0));
+  if (st != VR_OK) return st;
+  float* f = static_cast<float*>(ctx->out_staging);
+  st = render_common(ctx, params, f, nullptr, nullptr, 0, s);
+  if (st != VR_OK) return st;
+  uchar4* q = host_out ? reinterpret_cast<uchar4*>(static_cast<char*>(ctx->out_staging) + fbytes)
+                       : reinterpret_cast<uchar4*>(out_rgba8);
+  st = cuda_status(launch_quantize_rgba8(reinterpret_cast<const float4*>(f), q, npix, s));
+  if (st != VR_OK) return st;
+  if (host_out) st = cuda_status(cudaMemcpyAsync(out_rgba8, q, bbytes, cudaMemcpyDeviceToHost, s));
   return st;
 }
 

@@ -69,6 +69,8 @@ _SIGS = [
     ("vr_set_transfer_function", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     ("vr_set_camera", C.c_int, [C.c_void_p, C.POINTER(vr_camera)]),
     ("vr_render", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p, C.c_void_p]),
+    ("vr_render_rgba8", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_void_p,
+                                  C.c_void_p]),
     ("vr_render_rows", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_int, C.c_int,
                                  C.c_void_p, C.c_void_p]),
     ("vr_render_partial", C.c_int, [C.c_void_p, C.POINTER(vr_render_params), C.c_float,
@@ -268,6 +270,14 @@ def vr_set_camera(ctx, cam):
 def vr_render(ctx, params, out_rgba, stream=None):
     _buf("vr_render", out_rgba, _state.get(ctx, {}).get("image", 0), 4, what="out_rgba")
     _check("vr_render", lib().vr_render(ctx, C.byref(params), _ptr(out_rgba), stream))
+
+
+def vr_render_rgba8(ctx, params, out_rgba8, stream=None):
+    """vr_render's image with 8 bits per channel into an H x W x 4 byte buffer."""
+    _buf("vr_render_rgba8", out_rgba8, _state.get(ctx, {}).get("image", 0) // 4, 1,
+         what="out_rgba8")
+    _check("vr_render_rgba8", lib().vr_render_rgba8(ctx, C.byref(params), _ptr(out_rgba8),
+                                                    stream))
 
 
 def vr_render_rows(ctx, params, row0, row1, out_rgba, stream=None):

@@ -63,6 +63,7 @@ def test_null_arguments_are_rejected_without_a_device(libvr):
     assert L.vr_set_camera(None, None) == 1
     p = vr.make_params()
     assert L.vr_render(None, C.byref(p), None, None) == 1
+    assert L.vr_render_rgba8(None, C.byref(p), None, None) == 1
     assert L.vr_render_backward(None, C.byref(p), None, None, None, None, None) == 1
     assert L.vr_read_stats(None, None, None) == 1
     pk = vr.vr_peaks()
@@ -127,6 +128,8 @@ def test_binding_checks_buffers_before_calling_the_library(libvr):
 
     # transposed (non-contiguous) image
     rejected(vr.vr_render, None, p, torch.zeros(6, 8, 4).transpose(0, 1))
+    # the 8-bit image takes 1-byte elements
+    rejected(vr.vr_render_rgba8, None, p, torch.zeros(6, 8, 4))
     # voxels: too few bytes for 4 x 4 x 4 u16, and u16 voxels given as float32
     rejected(vr.vr_upload_volume, None, np.zeros(60, np.uint16), "u16", 4, 4, 4, 4095.0)
     rejected(vr.vr_upload_volume, None, np.zeros(64, np.float32), "u16", 4, 4, 4, 4095.0)
